@@ -1,0 +1,119 @@
+"""Pins of the oracle's sequential movement phase and whole steps.
+
+Hand-built scenes where the order decides the outcome (the order recomputed
+independently from Philox), invariants of many steps (occupancy is a bijection
+with the agents present, no agent on a wall or exit, agents conserved except
+through exits), independence from storage order and thread count, and the
+paper's OpenMP partition.
+"""
+import numpy as np
+import pytest
+
+from paper_0911_2900_gb300 import workloads as wl
+from tests import refs
+
+
+def _corridor(W=12):
+    t = np.full((3, W), wl.WALL, np.uint8)
+    t[1, 1:W - 1] = wl.FREE
+    t[1, W - 1] = wl.EXIT
+    return t
+
+
+def test_order_decides_follow_or_block(orc):
+    """A at x=3 wants x=5, B at x=4 wants x=6 (v=2).  If B moves first, A
+    follows to x=5; if A moves first it is blocked by B and stays at x=3."""
+    t = _corridor()
+    W = t.shape[1]
+    for seed in range(40):
+        sim = orc.Sim(t, v=2, kS=1.2, seed=seed)
+        A, B = 1 * W + 3, 1 * W + 4
+        sim.place([A, B], ids=[0, 1])
+        desired = np.array([1 * W + 5, 1 * W + 6], np.int32)
+        sim.move(desired, t=7)
+        pA = refs.move_priority(seed, 0, 7)
+        pB = refs.move_priority(seed, 1, 7)
+        if pB < pA:
+            assert sim.cell.tolist() == [1 * W + 5, 1 * W + 6]
+        else:
+            assert sim.cell.tolist() == [1 * W + 3, 1 * W + 6]
+
+
+def test_exit_removes_agent_and_frees_cell(orc):
+    t = _corridor(8)
+    W = 8
+    sim = orc.Sim(t, v=3, kS=1.2, seed=0)
+    sim.place([1 * W + 5, 1 * W + 2], ids=[0, 1])
+    # agent 0 walks through the exit cell at x=7 (path stops there); agent 1
+    # wants x=5, which agent 0 frees whatever the order (it never blocks x=5
+    # after leaving, and if agent 1 goes first it stops at x=4)
+    desired = np.array([1 * W + 7, 1 * W + 5], np.int32)
+    left = sim.move(desired, t=0)
+    assert left == 1
+    assert sim.cell[0] == -1
+    assert sim.occ[1 * W + 7] == -1 and sim.occ[1 * W + 5] in (-1, 1)
+    p0, p1 = refs.move_priority(0, 0, 0), refs.move_priority(0, 1, 0)
+    assert sim.cell[1] == (1 * W + 5 if p0 < p1 else 1 * W + 4)
+
+
+def test_priority_matches_reference(orc):
+    for seed in (0, 1, 2 ** 40 + 17):
+        for i in range(50):
+            for t in (0, 1, 395):
+                assert orc.move_priority(seed, i, t) == refs.move_priority(seed, i, t)
+
+
+def _check_invariants(sim, n0, exited):
+    occ = sim.occ
+    alive = sim.cell >= 0
+    assert alive.sum() + exited == n0
+    cells = sim.cell[alive]
+    assert len(np.unique(cells)) == len(cells)
+    assert (sim.type.ravel()[cells] == wl.FREE).all()
+    # occupancy is a bijection with the agents present
+    idx = np.flatnonzero(occ >= 0)
+    assert len(idx) == alive.sum()
+    assert (sim.cell[occ[idx]] == idx).all()
+    assert ((occ == -2) == (sim.type.ravel() == wl.WALL)).all()
+
+
+@pytest.mark.parametrize("v", [1, 3, 5])
+def test_invariants_over_many_steps(orc, v):
+    w = wl.config_small_room(W=60, H=50, n=600, seed=v, v_m=v)
+    sim = orc.Sim(w.cell_type, v=v, kS=1.2, seed=v)
+    sim.place(w.cells)
+    exited = 0
+    for t in range(120):
+        d = sim.plan(t)
+        exited += sim.move(d, t)
+        _check_invariants(sim, len(w.cells), exited)
+    assert exited > 0
+
+
+def test_storage_order_and_threads_do_not_matter(orc):
+    w = wl.config_small_room(W=80, H=60, n=1500, seed=3, v_m=4)
+    ref = orc.Sim(w.cell_type, v=4, kS=1.2, seed=11)
+    ref.place(w.cells)
+    out_ref = ref.run(0, 30, threads=1)
+    perm = np.random.default_rng(0).permutation(len(w.cells))
+    shuf = orc.Sim(w.cell_type, v=4, kS=1.2, seed=11, S=ref.S)
+    shuf.place(w.cells[perm], ids=perm.astype(np.int32))
+    out_shuf = shuf.run(0, 30, threads=4)
+    assert np.array_equal(out_ref["dig_cell"], out_shuf["dig_cell"])
+    assert np.array_equal(out_ref["dig_des"], out_shuf["dig_des"])
+    assert np.array_equal(ref.cells_by_id(), shuf.cells_by_id())
+
+
+def test_openmp_partition_matches_serial(orc):
+    w = wl.config_small_room(W=100, H=100, n=4000, seed=1, v_m=4)
+    s1 = orc.Sim(w.cell_type, v=4, kS=1.2, seed=2)
+    s1.place(w.cells)
+    d1 = s1.plan(5, threads=1)
+    d8 = s1.plan(5, threads=8)
+    assert np.array_equal(d1, d8)
+
+
+def test_digest_skips_absent_agents(orc):
+    ids = np.arange(5, dtype=np.int32)
+    vals = np.array([3, -1, 7, -1, 9], np.int32)
+    assert orc.digest(ids, vals) == orc.digest(ids[[0, 2, 4]], vals[[0, 2, 4]])
