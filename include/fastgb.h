@@ -1,0 +1,199 @@
+/*
+ * fastgb.h -- C ABI of libfastgb: the time step of the F.A.S.T. pedestrian
+ * model (T. Kretz, "Computation Speed of the F.A.S.T. Model", arXiv:0911.2900)
+ * on one NVIDIA GB300 GPU.
+ *
+ * A time step is a planning phase in which every agent chooses a desired cell
+ * from data common to all agents, which it only reads, followed by a movement
+ * phase that is sequential, agent after agent, so that no two agents ever
+ * share a cell (Sec. 1).  The model parameters are k_S = 1.2, k_other = 0 and
+ * one maximum speed v_m for all agents of a simulation; one step is one
+ * simulated second (Sec. 2).  The paper does not restate the model's rules;
+ * this library fixes them as follows (the same rules as the FP64 reference
+ * the tests compare against):
+ *   - floor field S: shortest 8-neighbour path to any exit cell through
+ *     non-wall cells, costs 1 and sqrt(2), kept exactly as a + b*sqrt(2);
+ *   - candidates of an agent on cell c0: offsets (dx,dy) of the reach set
+ *     (dx^2+dy^2 <= v_m^2 by default), in row order, inside the grid, whose
+ *     straight path has no wall, whose target is free or is c0 itself;
+ *   - weight exp(-k_S (S(c) - S(c0))), summed in that order in FP64; the
+ *     choice is the smallest k with u*W < C_k, u a 53-bit uniform from
+ *     Philox4x32-10 (key = seed, counter = (id, step, 0, 0));
+ *   - movement in ascending order of (top 40 bits of Philox(id, step, 1, 0),
+ *     id); each agent walks its straight path, stops before a blocked cell,
+ *     leaves on entering an exit cell.
+ *
+ * Conventions for every call:
+ *   - cells are row-major indices y*width + x; cell types are 0 free, 1 wall,
+ *     2 exit;
+ *   - host pointers are borrowed for the duration of the call and copied;
+ *   - device memory is owned by the context; it comes from the allocator
+ *     callbacks given to fast_create (or cudaMalloc when they are NULL);
+ *   - work is queued on the CUDA stream given to fast_create; calls that
+ *     return data to the host synchronise that stream;
+ *   - the return value is FAST_OK (0) or a negative FAST_E* code, with a
+ *     message in fast_last_error(); after FAST_ECUDA or FAST_ETIMEOUT the
+ *     context is poisoned and only fast_last_error / fast_destroy are valid.
+ */
+#ifndef FASTGB_H
+#define FASTGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FAST_OK 0
+#define FAST_EINVAL (-1)   /* bad argument: shape, cell, id, v_m, ...        */
+#define FAST_ESTATE (-2)   /* call out of order (e.g. step before placement) */
+#define FAST_ENOMEM (-3)   /* device allocation failed                      */
+#define FAST_ECUDA (-4)    /* CUDA runtime error                            */
+#define FAST_ETIMEOUT (-5) /* a bounded device-side wait gave up            */
+
+/* precision of the planning phase */
+#define FAST_FP64 0           /* every agent with the FP64 rule               */
+#define FAST_FP32_RECHECK 1   /* FP32 weights; draws near a boundary in FP64   */
+#define FAST_FP32_NORECHECK 2 /* FP32 only (diagnostic: may differ from FP64)  */
+
+/* reach set of one step */
+#define FAST_REACH_L2 0   /* dx^2 + dy^2 <= v^2        (K = 5,13,29,49,81)   */
+#define FAST_REACH_L2P 1  /* dx^2 + dy^2 <= v^2 + v    (K = 9,21,37,69,97)   */
+#define FAST_REACH_LINF 2 /* max(|dx|,|dy|) <= v       (K = 9,25,49,81,121)  */
+
+#define FAST_CELL_FREE 0
+#define FAST_CELL_WALL 1
+#define FAST_CELL_EXIT 2
+
+/* options for fast_set_option */
+#define FAST_OPT_RESORT_PERIOD 1  /* re-sort agents in Morton order every n steps (default 8; 0 never) */
+#define FAST_OPT_DIGESTS 2        /* 1: record per-step digests (fast_get_digests)  */
+#define FAST_OPT_LANES_V1 3       /* lanes per agent of the FP32 kernel for v_m=1; */
+                                  /* ..._V1 + (v_m - 1) for v_m = 1..5; 1,2,4,8    */
+#define FAST_OPT_BARRIER_NS 10    /* time limit of one device-side wait, ns         */
+#define FAST_OPT_USE_GRAPH 11     /* 1 (default): steps replay a captured CUDA graph */
+#define FAST_OPT_MOVE_BLOCKS 12   /* blocks of the cooperative movement kernel (0: auto) */
+#define FAST_OPT_TILE_SHIFT 13    /* Morton bucket side = 2^shift cells (default 4) */
+
+typedef struct fast_ctx fast_ctx;
+
+/* Device allocator callbacks: alloc returns a device pointer of >= bytes
+ * (256-byte aligned) or NULL; free releases it.  `user` is passed through. */
+typedef void* (*fast_alloc_fn)(size_t bytes, void* user);
+typedef void (*fast_free_fn)(void* ptr, void* user);
+
+/* One replicate's grid. */
+typedef struct {
+  int32_t width, height;    /* cells; width*height < 2^31                   */
+  const uint8_t* cell_type; /* host [width*height], borrowed for the call    */
+  double k_S;               /* coupling to the static floor field (>= 0)     */
+  int32_t v_m;              /* maximum speed, 1..5 cells per step            */
+  uint64_t seed;            /* Philox key of this replicate                  */
+} fast_grid_desc;
+
+typedef struct {
+  int64_t step;            /* index of the next step                            */
+  int64_t steps_run;       /* steps run since the last placement                */
+  int32_t alive;           /* agents of this replicate still in the simulation  */
+  int32_t exited;          /* agents of this replicate that left through an exit */
+  int64_t agent_steps;     /* all replicates: sum over steps of agents planned  */
+  int64_t rechecked;       /* all replicates: draws re-evaluated in FP64        */
+  int64_t move_rounds;     /* all replicates: movement rounds, total            */
+  int32_t max_rounds;      /* largest number of movement rounds in one step     */
+  int32_t last_rounds;     /* movement rounds of the last step                  */
+  int64_t kernel_launches; /* CUDA kernels this context has queued, in total    */
+} fast_stats;
+
+typedef struct {
+  int64_t agents;          /* agents evaluated                                  */
+  int64_t flagged;         /* FP32 draws inside the margin (re-checked in FP64) */
+  int64_t flips;           /* FP32 choice != FP64 choice                        */
+  int64_t flips_unflagged; /* of those, outside the margin (must be 0)          */
+  double max_abs_dp;       /* max |P32(k) - P64(k)| over cumulative probabilities */
+  double margin;           /* relative margin M of the FP32 decision           */
+} fast_precision_report;
+
+/* Creates a context for n_replicates independent replicates (1..256).
+ * precision: FAST_FP64 / FAST_FP32_RECHECK / FAST_FP32_NORECHECK;
+ * reach: FAST_REACH_*; cuda_stream: a cudaStream_t (NULL: legacy default).
+ * Errors: FAST_EINVAL, FAST_ECUDA (no device). */
+int fast_create(fast_ctx** out, int32_t n_replicates, int32_t precision, int32_t reach,
+                void* cuda_stream, fast_alloc_fn dev_alloc, fast_free_fn dev_free,
+                void* alloc_user);
+
+/* Sets the grid of one replicate: validates the cell types, computes the
+ * exact floor field on the host, uploads cell records and line-of-sight
+ * masks.  Every free cell that no exit can be reached from is treated as a
+ * wall.  Errors: FAST_EINVAL (types, size, v_m, k_S, no exit, distance too
+ * long for the 15-bit record fields), FAST_ENOMEM, FAST_ECUDA. */
+int fast_init_grid(fast_ctx* ctx, int32_t replicate, const fast_grid_desc* grid);
+
+/* Places n agents of one replicate (replacing any previous ones).
+ * cells: host [n] distinct free, reachable, non-exit cells (NULL: error);
+ * ids: host [n] distinct ids in [0, 2^24) (NULL: 0..n-1);
+ * start_step: index of the next step (all replicates share one step index;
+ * resuming a run = placing its read-back state with its step index).
+ * Errors: FAST_EINVAL, FAST_ESTATE (grid not set), FAST_ENOMEM, FAST_ECUDA. */
+int fast_place_agents(fast_ctx* ctx, int32_t replicate, int32_t n, const int32_t* cells,
+                      const int32_t* ids, int32_t start_step);
+
+/* Queues n_steps full steps (planning + movement) of every replicate on the
+ * context's stream; returns without waiting.  Errors: FAST_ESTATE, FAST_ECUDA. */
+int fast_step(fast_ctx* ctx, int32_t n_steps);
+
+/* Queues n planning passes only (no movement, the step index does not move):
+ * used to time the planning phase alone. */
+int fast_plan_only(fast_ctx* ctx, int32_t n);
+
+/* Waits for the stream, then writes, for ids 0..id_bound-1, the cell of each
+ * agent of the replicate (-1: left or not present) and its desired cell of
+ * the last planning pass (-1 likewise); either pointer may be NULL.  stats may
+ * be NULL.  Errors: FAST_EINVAL, FAST_ETIMEOUT / FAST_ECUDA (device error). */
+int fast_readback(fast_ctx* ctx, int32_t replicate, int32_t id_bound, int32_t* cells_by_id,
+                  int32_t* desired_by_id, fast_stats* stats);
+
+/* Per-step digests recorded since the last placement while FAST_OPT_DIGESTS
+ * is on: sum over agents still present of splitmix64(id << 32 | cell) after
+ * the step's movement, and of splitmix64(id << 32 | desired) after its
+ * planning.  Writes min(max_steps, recorded) values; returns that count or a
+ * negative error. */
+int fast_get_digests(fast_ctx* ctx, int32_t replicate, int32_t max_steps, uint64_t* cell_digest,
+                     uint64_t* desired_digest);
+
+/* Device times (ms) of the parts of the last step queued by fast_step, from
+ * CUDA events recorded on the context's stream (waits for them):
+ * ms4[0] planning kernels, ms4[1] FP64 re-check, ms4[2] movement (footprints
+ * and rounds), ms4[3] bookkeeping (digests, re-sort, step counter).
+ * Errors: FAST_ESTATE if no step has run. */
+int fast_phase_times(fast_ctx* ctx, float* ms4);
+
+/* Runs the FP32 planning of the current state without re-check next to the
+ * FP64 rule and compares them (does not change the state).  Errors:
+ * FAST_ESTATE (precision is FAST_FP64 or no agents), FAST_ENOMEM, FAST_ECUDA. */
+int fast_precision_report_run(fast_ctx* ctx, fast_precision_report* out);
+
+/* Number of distinct cells whose record one planning pass of the replicate
+ * reads (own cells and line-of-sight reach offsets), for byte accounting. */
+int fast_reach_union(fast_ctx* ctx, int32_t replicate, int64_t* cells);
+
+int fast_set_option(fast_ctx* ctx, int32_t option, int64_t value);
+const char* fast_last_error(const fast_ctx* ctx);
+void fast_destroy(fast_ctx* ctx);
+
+/* ---- self tests of the device arithmetic (need a GPU; no context) -------- */
+/* y[i] = the library's FP64 exponential of x[i] on the GPU; host arrays [n]. */
+int fast_selftest_exp64(const double* x, double* y, int64_t n);
+/* Philox4x32-10 on the GPU: ctr [4n], key [2n], out [4n], host arrays. */
+int fast_selftest_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n);
+/* Largest relative error of the SFU 2^y over every float y in [lo, hi]. */
+int fast_selftest_ex2(float lo, float hi, double* max_rel_err);
+/* Runs a cooperative kernel whose grid barrier can never complete, with a
+ * wait limit of limit_ns; returns FAST_ETIMEOUT when the wait gave up (the
+ * expected outcome) and leaves the CUDA context usable. */
+int fast_selftest_barrier_timeout(int64_t limit_ns);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

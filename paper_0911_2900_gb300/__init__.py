@@ -1,1 +1,284 @@
-"""GB300 implementation of the F.A.S.T. time step (binding added with the CUDA library)."""
+"""Python binding of libfastgb, the GB300 implementation of the F.A.S.T. time step.
+
+Argument marshalling only: every step of the planning and movement phases runs
+in the CUDA kernels of ``csrc/`` behind the C ABI of ``include/fastgb.h``.  There
+is no CPU fallback: if the shared library cannot be loaded (not built, or no
+CUDA device), the calls raise.
+
+PyTorch is used only as the device allocator and to supply the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["Context", "FastError", "load", "PRECISION", "REACH", "OPT"]
+
+PRECISION = {"fp64": 0, "fp32_recheck": 1, "fp32_norecheck": 2}
+REACH = {"l2": 0, "l2p": 1, "linf": 2}
+OPT = {"resort_period": 1, "digests": 2, "lanes_v1": 3, "lanes_v2": 4, "lanes_v3": 5,
+       "lanes_v4": 6, "lanes_v5": 7, "barrier_ns": 10, "use_graph": 11, "move_blocks": 12,
+       "tile_shift": 13}
+ERRORS = {0: "FAST_OK", -1: "FAST_EINVAL", -2: "FAST_ESTATE", -3: "FAST_ENOMEM",
+          -4: "FAST_ECUDA", -5: "FAST_ETIMEOUT"}
+
+
+class FastError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("cell_type", C.c_void_p),
+                ("k_S", C.c_double), ("v_m", C.c_int32), ("seed", C.c_uint64)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("step", C.c_int64), ("steps_run", C.c_int64), ("alive", C.c_int32),
+                ("exited", C.c_int32), ("agent_steps", C.c_int64), ("rechecked", C.c_int64),
+                ("move_rounds", C.c_int64), ("max_rounds", C.c_int32), ("last_rounds", C.c_int32),
+                ("kernel_launches", C.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class PrecisionReport(C.Structure):
+    _fields_ = [("agents", C.c_int64), ("flagged", C.c_int64), ("flips", C.c_int64),
+                ("flips_unflagged", C.c_int64), ("max_abs_dp", C.c_double), ("margin", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+
+EXPORTS = {
+    "fast_create": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_void_p]),
+    "fast_init_grid": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "fast_place_agents": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                    C.c_int32]),
+    "fast_step": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fast_plan_only": (C.c_int, [C.c_void_p, C.c_int32]),
+    "fast_readback": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
+                                C.c_void_p]),
+    "fast_get_digests": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
+    "fast_phase_times": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fast_precision_report_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fast_reach_union": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "fast_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "fast_last_error": (C.c_char_p, [C.c_void_p]),
+    "fast_destroy": (None, [C.c_void_p]),
+    "fast_selftest_exp64": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
+    "fast_selftest_philox": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
+    "fast_selftest_ex2": (C.c_int, [C.c_float, C.c_float, C.c_void_p]),
+    "fast_selftest_barrier_timeout": (C.c_int, [C.c_int64]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Loads libfastgb.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                _build.build()
+            if not os.path.exists(_build.LIB):
+                raise FastError(-4, f"libfastgb.so not built ({_build.LIB})")
+            lib = C.CDLL(_build.LIB)
+            for name, (res, args) in EXPORTS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, kept alive by pointer."""
+
+    def __init__(self, device):
+        import torch
+
+        self.torch = torch
+        self.device = device
+        self.live = {}
+        self.alloc_cb = ALLOC_FN(self._alloc)
+        self.free_cb = FREE_FN(self._free)
+
+    def _alloc(self, nbytes, _user):
+        try:
+            t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
+        except Exception:  # out of memory: the library reports FAST_ENOMEM
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, ptr, _user):
+        self.live.pop(ptr, None)
+
+
+class Context:
+    """One fast_ctx: n replicates stepped together on one CUDA stream."""
+
+    def __init__(self, n_replicates: int = 1, precision: str = "fp32_recheck",
+                 reach: str = "l2", stream=None, device=None, torch_memory: bool = True):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise FastError(-4, "no CUDA device: libfastgb runs on the GPU only")
+        self.lib = load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+        self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
+        self._alloc = _TorchAllocator(self.device) if torch_memory else None
+        h = C.c_void_p()
+        rc = self.lib.fast_create(
+            C.byref(h), n_replicates, PRECISION[precision], REACH[reach],
+            C.c_void_p(self.stream.cuda_stream),
+            C.cast(self._alloc.alloc_cb, C.c_void_p) if self._alloc else None,
+            C.cast(self._alloc.free_cb, C.c_void_p) if self._alloc else None, None)
+        if rc != 0:
+            raise FastError(rc, "fast_create failed")
+        self.h = h
+        self.n_rep = n_replicates
+        self.precision = precision
+        self.reach = reach
+        self.id_bound = [0] * n_replicates
+
+    # -- helpers ---------------------------------------------------------------
+    def _check(self, rc, what):
+        if rc < 0:
+            msg = self.lib.fast_last_error(self.h)
+            raise FastError(rc, f"{what}: {msg.decode() if msg else ''}")
+        return rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.fast_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API ---------------------------------------------------------------------
+    def init_grid(self, rep: int, cell_type: np.ndarray, k_S: float = 1.2, v_m: int = 4,
+                  seed: int = 0):
+        t = np.ascontiguousarray(cell_type, dtype=np.uint8)
+        H, W = t.shape
+        g = GridDesc(W, H, t.ctypes.data, float(k_S), int(v_m), int(seed))
+        self._check(self.lib.fast_init_grid(self.h, rep, C.byref(g)), "fast_init_grid")
+
+    def place(self, rep: int, cells, ids=None, start_step: int = 0):
+        c = np.ascontiguousarray(cells, dtype=np.int32)
+        i = None if ids is None else np.ascontiguousarray(ids, dtype=np.int32)
+        self._check(self.lib.fast_place_agents(self.h, rep, len(c), _ptr(c), _ptr(i),
+                                               int(start_step)), "fast_place_agents")
+        self.id_bound[rep] = (int(i.max()) + 1 if len(c) else 0) if i is not None else len(c)
+
+    def step(self, n: int = 1):
+        self._check(self.lib.fast_step(self.h, int(n)), "fast_step")
+
+    def plan_only(self, n: int = 1):
+        self._check(self.lib.fast_plan_only(self.h, int(n)), "fast_plan_only")
+
+    def readback(self, rep: int = 0, id_bound: int | None = None, cells_out=None,
+                 desired_out=None):
+        """Returns (cells_by_id, desired_by_id, stats dict); -1 = not present."""
+        b = self.id_bound[rep] if id_bound is None else int(id_bound)
+        cells = np.empty(b, np.int32) if cells_out is None else cells_out
+        des = np.empty(b, np.int32) if desired_out is None else desired_out
+        st = Stats()
+        self._check(self.lib.fast_readback(self.h, rep, b, _ptr(cells), _ptr(des), C.byref(st)),
+                    "fast_readback")
+        return cells, des, st.as_dict()
+
+    def digests(self, rep: int, max_steps: int):
+        a = np.zeros(max_steps, np.uint64)
+        b = np.zeros(max_steps, np.uint64)
+        n = self._check(self.lib.fast_get_digests(self.h, rep, max_steps, _ptr(a), _ptr(b)),
+                        "fast_get_digests")
+        return a[:n], b[:n]
+
+    def phase_times(self):
+        """(planning kernels, FP64 re-check, movement, bookkeeping) of the last step, ms."""
+        ms = (C.c_float * 4)()
+        self._check(self.lib.fast_phase_times(self.h, ms), "fast_phase_times")
+        return tuple(ms)
+
+    def precision_report(self):
+        r = PrecisionReport()
+        self._check(self.lib.fast_precision_report_run(self.h, C.byref(r)),
+                    "fast_precision_report_run")
+        return r.as_dict()
+
+    def reach_union(self, rep: int = 0) -> int:
+        v = C.c_int64()
+        self._check(self.lib.fast_reach_union(self.h, rep, C.byref(v)), "fast_reach_union")
+        return v.value
+
+    def set_option(self, name: str, value: int):
+        self._check(self.lib.fast_set_option(self.h, OPT[name], int(value)), "fast_set_option")
+
+
+# -- self tests of the device arithmetic ------------------------------------------
+def selftest_exp64(x: np.ndarray) -> np.ndarray:
+    lib = load()
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty_like(x)
+    rc = lib.fast_selftest_exp64(_ptr(x), _ptr(y), len(x))
+    if rc:
+        raise FastError(rc, "fast_selftest_exp64")
+    return y
+
+
+def selftest_philox(ctr: np.ndarray, key: np.ndarray) -> np.ndarray:
+    lib = load()
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, np.uint32).reshape(-1, 2)
+    out = np.empty_like(c)
+    rc = lib.fast_selftest_philox(_ptr(c), _ptr(k), _ptr(out), len(c))
+    if rc:
+        raise FastError(rc, "fast_selftest_philox")
+    return out
+
+
+def selftest_ex2(lo: float, hi: float) -> float:
+    lib = load()
+    v = C.c_double()
+    rc = lib.fast_selftest_ex2(C.c_float(lo), C.c_float(hi), C.byref(v))
+    if rc:
+        raise FastError(rc, "fast_selftest_ex2")
+    return v.value
+
+
+def selftest_barrier_timeout(limit_ns: int = 1_000_000) -> int:
+    return load().fast_selftest_barrier_timeout(int(limit_ns))

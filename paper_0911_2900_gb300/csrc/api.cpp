@@ -1,0 +1,1082 @@
+// api.cpp -- host side of libfastgb: the C ABI declared in include/fastgb.h.
+//
+// Owns the context (replicates, device buffers, work chunks, the captured
+// CUDA graph of one step) and validates every input before anything reaches
+// the GPU.  All arithmetic of the step runs in the kernels of plan.cu,
+// move.cu and aux.cu; the host only computes the exact floor field at grid
+// set-up (floor_field.cpp) and checks placements.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "fast_internal.h"
+#include "fastgb.h"
+
+namespace fastgb {
+int64_t exact_floor_field(int32_t W, int32_t H, const uint8_t* type, int32_t* a, int32_t* b);
+}
+
+using namespace fastgb;
+
+namespace {
+
+// Largest relative error of one SFU 2^y used in the FP32 margin (covers the
+// measured maximum of ex2.approx.ftz.f32 over the argument range with a
+// factor of two to spare; see the self test fast_selftest_ex2).
+constexpr double kEx2RelErr = 0x1p-21;
+constexpr int kDefaultLanes[5] = {1, 2, 2, 4, 4};
+constexpr double kSqrt2 = 1.4142135623730951;
+constexpr double kLn2 = 0.6931471805599453;
+constexpr double kLog2e = 1.4426950408889634;
+
+struct RepHost {
+  bool grid_set = false;
+  bool placed = false;
+  int32_t W = 0, H = 0, v = 0, K = 0, mw = 1;
+  double kS = 0.0;
+  uint64_t seed = 0;
+  std::vector<uint8_t> placeable;  // free and reachable
+  std::vector<uint8_t> seen;       // duplicate check scratch
+  int32_t cap = 0;                 // agent slots allocated
+  int32_t n = 0;                   // agents placed
+  int32_t id_bound = 0;            // max id + 1
+  RepDev d{};                      // device pointers and parameters
+};
+
+}  // namespace
+
+struct fast_ctx {
+  int32_t n_rep = 0, precision = 0, reach = 0;
+  cudaStream_t stream = nullptr;      // the caller's stream: all work runs here
+  cudaStream_t cap_stream = nullptr;  // private stream the step graph is captured on
+  cudaStream_t cur = nullptr;         // where enqueue_* put their work
+  fast_alloc_fn alloc = nullptr;
+  fast_free_fn release = nullptr;
+  void* user = nullptr;
+  std::string err;
+  bool poisoned = false;
+  int sms = 0;
+  std::vector<RepHost> reps;
+  std::unordered_map<void*, size_t> live;  // allocations
+
+  // device-resident shared state
+  RepDev* d_reps = nullptr;
+  Ctl* d_ctl = nullptr;
+  int32_t* d_nslots = nullptr;
+  int32_t* d_exited = nullptr;
+  uint32_t* d_queue = nullptr;
+  uint32_t* d_act[3] = {nullptr, nullptr, nullptr};
+  uint32_t list_cap = 0;
+  uint32_t* d_bucket = nullptr;
+  int32_t n_buckets = 0;
+  size_t bucket_words = 0;
+  unsigned long long* d_dig_cell = nullptr;
+  unsigned long long* d_dig_des = nullptr;
+  int32_t dig_cap = 0;
+  int32_t* d_gather = nullptr;
+  int32_t gather_cap = 0;
+
+  struct Group {
+    int v = 0;
+    int n = 0;
+    int32_t* d_rep = nullptr;
+    int32_t* d_begin = nullptr;
+  };
+  std::vector<Group> groups;
+  int32_t* d_all_rep = nullptr;
+  int32_t* d_all_begin = nullptr;
+  int all_n = 0;
+  bool layout_dirty = true;
+
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int graph_state[2] = {0, 0};  // 0 not built, 1 built, 2 capture failed
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool ran_step = false;
+  int64_t launches = 0;          // kernels queued by this context
+  int launches_per_graph[2] = {0, 0};
+
+  // options
+  int resort_period = 8;
+  bool digests = false;
+  int lanes[5] = {1, 2, 2, 4, 4};
+  long long barrier_ns = 2000000000ll;
+  bool use_graph = true;
+  int move_blocks = 0;
+  int tile_shift = 4;
+
+  int64_t t_host = 0;
+  int64_t steps_since_place = 0;
+};
+
+// ---------------------------------------------------------------------------
+namespace {
+
+int fail(fast_ctx* c, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) {
+    c->err = buf;
+    if (code == FAST_ECUDA || code == FAST_ETIMEOUT) c->poisoned = true;
+  }
+  return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                               \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(ctx, FAST_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                              \
+  } while (0)
+
+#define LAUNCH_TRY(ctx, call)                                                        \
+  do {                                                                               \
+    (ctx)->launches += 1;                                                            \
+    int r_ = (call);                                                                 \
+    cudaError_t e_ = cudaGetLastError();                                             \
+    if (r_ != 0 || e_ != cudaSuccess)                                                \
+      return fail(ctx, FAST_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+  } while (0)
+
+void* dalloc(fast_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~(size_t)255;
+  void* p = nullptr;
+  if (c->alloc) {
+    p = c->alloc(bytes, c->user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->live[p] = bytes;
+  return p;
+}
+
+void dfree(fast_ctx* c, void* p) {
+  if (!p) return;
+  auto it = c->live.find(p);
+  if (it == c->live.end()) return;
+  c->live.erase(it);
+  if (c->release)
+    c->release(p, c->user);
+  else
+    cudaFree(p);
+}
+
+template <typename T>
+int alloc_into(fast_ctx* c, T** out, size_t count) {
+  *out = (T*)dalloc(c, count * sizeof(T));
+  if (!*out) return fail(c, FAST_ENOMEM, "device allocation of %zu bytes failed", count * sizeof(T));
+  return FAST_OK;
+}
+
+int reach_count_host(int v, int reach) {
+  int k = 0;
+  for (int y = -v; y <= v; ++y)
+    for (int x = -v; x <= v; ++x) {
+      const int r2 = x * x + y * y;
+      const bool in = reach == FAST_REACH_L2    ? r2 <= v * v
+                      : reach == FAST_REACH_L2P ? r2 <= v * v + v
+                                                : (std::abs(x) <= v && std::abs(y) <= v);
+      k += in ? 1 : 0;
+    }
+  return k;
+}
+
+// Relative margin M of the FP32 decision (see the comment of k_plan_fp32).
+// One weight 2^y, y = fl(fl(dS) * fl(-k_S log2 e)):
+//   |dS32 - dS| <= 2^-23 (v sqrt2 + 0.002)       (exact integers a, b; sqrt2
+//                                                  split in two floats)
+//   |y32 - y|   <= |c| |dS32 - dS| + |y|max 2^-22  (constant and product rounding)
+//   delta       = 2^{|y32 - y|} - 1 + e_ex2 + 2^-24
+// A cumulative value is a sum of at most K such weights in some order:
+//   gamma = (1 + delta)(1 + 2^-24)^K - 1.
+// |C32/W32 - C*/W*| <= 2 gamma / (1 - gamma) for the FP32 side and 2A for the
+// FP64 side (A = 1e-10 bounds the FP64 rule's own error against exact
+// arithmetic); the test itself and u -> float add 2^-21.  M doubles the sum.
+float margin_of(int v, int K, double kS) {
+  const double u24 = std::ldexp(1.0, -24);
+  const double ds_err = std::ldexp(1.0, -23) * (v * kSqrt2 + 0.002);
+  const double c = kS * kLog2e;
+  const double ymax = c * v * kSqrt2;
+  const double y_err = c * ds_err + ymax * std::ldexp(1.0, -22);
+  const double delta = std::expm1(kLn2 * y_err) + kEx2RelErr + u24;
+  const double gamma = (1.0 + delta) * std::pow(1.0 + u24, K) - 1.0;
+  const double A = 1e-10;
+  const double M = 2.0 * (4.0 * gamma / (1.0 - gamma) + std::ldexp(1.0, -21) + 2.0 * A);
+  return (float)M;
+}
+
+bool rep_ok(fast_ctx* c, int32_t r) { return c && r >= 0 && r < c->n_rep; }
+
+int upload_reps(fast_ctx* c) {
+  std::vector<RepDev> h(c->n_rep);
+  for (int r = 0; r < c->n_rep; ++r) h[r] = c->reps[r].d;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_reps, h.data(), sizeof(RepDev) * c->n_rep,
+                              cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FAST_OK;
+}
+
+void drop_graphs(fast_ctx* c) {
+  for (int i = 0; i < 2; ++i) {
+    if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+    c->graph[i] = nullptr;
+    c->graph_state[i] = 0;
+  }
+}
+
+// Work chunks (replicate, first slot) per v_m group and over all replicates;
+// Morton bucket ranges; shared lists sized for all agent slots.
+int rebuild_layout(fast_ctx* c) {
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  for (auto& g : c->groups) {
+    dfree(c, g.d_rep);
+    dfree(c, g.d_begin);
+  }
+  c->groups.clear();
+  dfree(c, c->d_all_rep);
+  dfree(c, c->d_all_begin);
+  c->d_all_rep = c->d_all_begin = nullptr;
+
+  std::vector<int32_t> all_r, all_b;
+  uint64_t total_cap = 0;
+  int64_t bucket_base = 0;
+  for (int r = 0; r < c->n_rep; ++r) {
+    RepHost& R = c->reps[r];
+    if (!R.grid_set) continue;
+    const int ts = c->tile_shift;
+    const int tx = (R.W + (1 << ts) - 1) >> ts, ty = (R.H + (1 << ts) - 1) >> ts;
+    int side = 1;
+    while (side < std::max(tx, ty)) side <<= 1;
+    R.d.tile_shift = ts;
+    R.d.tiles_x = tx;
+    R.d.tiles_y = ty;
+    R.d.bucket_base = (int32_t)bucket_base;
+    R.d.bucket_span = side * side;
+    bucket_base += (int64_t)side * side;
+    if (!R.placed) continue;
+    total_cap += (uint64_t)R.cap;
+    for (int b = 0; b < R.cap; b += kChunk) {
+      all_r.push_back(r);
+      all_b.push_back(b);
+    }
+  }
+  if (bucket_base > (int64_t)1 << 30)
+    return fail(c, FAST_EINVAL, "too many Morton buckets (%lld); raise the tile shift",
+                (long long)bucket_base);
+  for (int v = 1; v <= 5; ++v) {
+    std::vector<int32_t> gr, gb;
+    for (int r = 0; r < c->n_rep; ++r) {
+      RepHost& R = c->reps[r];
+      if (!R.grid_set || !R.placed || R.v != v) continue;
+      for (int b = 0; b < R.cap; b += kChunk) {
+        gr.push_back(r);
+        gb.push_back(b);
+      }
+    }
+    if (gr.empty()) continue;
+    fast_ctx::Group g;
+    g.v = v;
+    g.n = (int)gr.size();
+    if (int e = alloc_into(c, &g.d_rep, gr.size())) return e;
+    if (int e = alloc_into(c, &g.d_begin, gb.size())) return e;
+    CUDA_TRY(c, cudaMemcpy(g.d_rep, gr.data(), gr.size() * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(g.d_begin, gb.data(), gb.size() * 4, cudaMemcpyHostToDevice));
+    c->groups.push_back(g);
+  }
+  c->all_n = (int)all_r.size();
+  if (c->all_n > 0) {
+    if (int e = alloc_into(c, &c->d_all_rep, all_r.size())) return e;
+    if (int e = alloc_into(c, &c->d_all_begin, all_b.size())) return e;
+    CUDA_TRY(c, cudaMemcpy(c->d_all_rep, all_r.data(), all_r.size() * 4, cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_all_begin, all_b.data(), all_b.size() * 4,
+                           cudaMemcpyHostToDevice));
+  }
+  if (total_cap > c->list_cap) {
+    dfree(c, c->d_queue);
+    for (auto& p : c->d_act) dfree(c, p);
+    c->d_queue = nullptr;
+    c->d_act[0] = c->d_act[1] = c->d_act[2] = nullptr;
+    const size_t n = (size_t)total_cap;
+    if (int e = alloc_into(c, &c->d_queue, n)) return e;
+    for (auto& p : c->d_act)
+      if (int e = alloc_into(c, &p, n)) return e;
+    c->list_cap = (uint32_t)total_cap;
+  }
+  const size_t words = (size_t)bucket_base + 1 + 2 * (size_t)c->n_rep;
+  if (words > c->bucket_words) {
+    dfree(c, c->d_bucket);
+    c->d_bucket = nullptr;
+    if (int e = alloc_into(c, &c->d_bucket, words)) return e;
+    c->bucket_words = words;
+  }
+  c->n_buckets = (int32_t)bucket_base;
+  if (int e = upload_reps(c)) return e;
+  c->layout_dirty = false;
+  return FAST_OK;
+}
+
+StepArgs args_of(fast_ctx* c) {
+  StepArgs a{};
+  a.reps = c->d_reps;
+  a.n_rep = c->n_rep;
+  a.ctl = c->d_ctl;
+  a.n_slots = c->d_nslots;
+  a.exited = c->d_exited;
+  a.queue = c->d_queue;
+  a.q_cap = c->list_cap;
+  for (int i = 0; i < 3; ++i) a.act[i] = c->d_act[i];
+  a.act_cap = c->list_cap;
+  a.dig_cell = c->d_dig_cell;
+  a.dig_des = c->d_dig_des;
+  a.dig_cap = c->dig_cap;
+  a.bucket_count = c->d_bucket;
+  a.n_buckets = c->n_buckets;
+  return a;
+}
+
+Chunks all_chunks(fast_ctx* c) { return Chunks{c->d_all_rep, c->d_all_begin, c->all_n}; }
+
+int plan_grid(fast_ctx* c, int n_chunks) { return std::max(1, std::min(n_chunks, c->sms * 8)); }
+
+int move_grid(fast_ctx* c) {
+  int g = 0;
+  if (move_rounds_max_grid(256, &g) != 0 || g <= 0) g = c->sms;
+  if (c->move_blocks > 0) g = std::min(g, c->move_blocks);
+  const int need = std::max(1, (int)((c->list_cap + 255) / 256));
+  g = std::min(g, std::max(need, 1));
+  g = std::min(g, c->sms * 2);
+  return std::max(g, 1);
+}
+
+// Inside a capture the record must be an external event-record node, so that
+// the event is really recorded each time the graph is replayed.
+cudaError_t record_event(fast_ctx* c, int i) {
+  return cudaEventRecordWithFlags(c->ev[i], c->cur,
+                                  c->cur == c->cap_stream ? cudaEventRecordExternal : 0);
+}
+
+int enqueue_plan(fast_ctx* c, const StepArgs& a, bool diag, bool events) {
+  for (auto& g : c->groups) {
+    Chunks ch{g.d_rep, g.d_begin, g.n};
+    LAUNCH_TRY(c, plan_groups_launch(a, g.v, c->reach, c->lanes[g.v - 1], c->precision, ch,
+                                     plan_grid(c, g.n), c->cur, diag));
+  }
+  if (events) CUDA_TRY(c, record_event(c, 1));
+  if (c->precision == FAST_FP32_RECHECK && !diag)
+    LAUNCH_TRY(c, plan_recheck_launch(a, std::max(1, c->sms), c->cur));
+  return FAST_OK;
+}
+
+// One step: planning kernels | FP64 re-check | movement (prep + rounds) |
+// bookkeeping; events ev[0..4] bracket the four parts.
+int enqueue_step(fast_ctx* c, bool resort) {
+  const StepArgs a = args_of(c);
+  const Chunks all = all_chunks(c);
+  CUDA_TRY(c, record_event(c, 0));
+  if (int e = enqueue_plan(c, a, false, true)) return e;
+  CUDA_TRY(c, record_event(c, 2));
+  if (c->digests) LAUNCH_TRY(c, digest_des_launch(a, all, plan_grid(c, all.n), c->cur));
+  LAUNCH_TRY(c, move_prep_launch(a, all, plan_grid(c, all.n), c->cur));
+  LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), 256, c->cur));
+  CUDA_TRY(c, record_event(c, 3));
+  if (c->digests) {
+    LAUNCH_TRY(c, digest_cell_launch(a, all, plan_grid(c, all.n), c->cur));
+    c->launches += 1;  // digest_cell_launch queues two kernels
+  }
+  if (resort) {
+    LAUNCH_TRY(c, resort_launch(a, all, plan_grid(c, all.n), false, c->cur));
+    c->launches += 5;  // resort_launch queues six kernels
+  }
+  LAUNCH_TRY(c, step_end_launch(a, c->cur));
+  CUDA_TRY(c, record_event(c, 4));
+  return FAST_OK;
+}
+
+// Captures one step on the private stream; the graph is then replayed on the
+// caller's stream.  If capture is not possible, steps are queued directly.
+int build_graph(fast_ctx* c, int which) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->graph_state[which] = 2;
+    return FAST_OK;
+  }
+  c->cur = c->cap_stream;
+  const int64_t before = c->launches;
+  const std::string err_before = c->err;
+  const int e = enqueue_step(c, which == 1);
+  c->cur = c->stream;
+  c->launches_per_graph[which] = (int)(c->launches - before);
+  c->launches = before;
+  cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+  if (e != FAST_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    c->poisoned = false;  // capture failure: fall back to direct launches
+    c->err = err_before;
+    c->graph_state[which] = 2;
+    return FAST_OK;
+  }
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    c->graph_state[which] = 2;
+    return FAST_OK;
+  }
+  cudaGraphDestroy(g);
+  c->graph[which] = ex;
+  c->graph_state[which] = 1;
+  return FAST_OK;
+}
+
+int write_ctl_int(fast_ctx* c, size_t offset, int32_t v) {
+  CUDA_TRY(c, cudaMemcpyAsync((char*)c->d_ctl + offset, &v, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FAST_OK;
+}
+
+int check_device_error(fast_ctx* c) {
+  Ctl h{};
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  CUDA_TRY(c, cudaMemcpy(&h, c->d_ctl, sizeof h, cudaMemcpyDeviceToHost));
+  if (h.err == kDevErrTimeout)
+    return fail(c, FAST_ETIMEOUT, "a device-side wait exceeded its limit (%lld ns)",
+                (long long)c->barrier_ns);
+  if (h.err != 0) return fail(c, FAST_ECUDA, "device error code %d", h.err);
+  return FAST_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+static int create_impl(fast_ctx* c, int32_t n_replicates);
+
+int fast_create(fast_ctx** out, int32_t n_replicates, int32_t precision, int32_t reach,
+                void* cuda_stream, fast_alloc_fn dev_alloc, fast_free_fn dev_free,
+                void* alloc_user) {
+  if (!out) return FAST_EINVAL;
+  *out = nullptr;
+  if (n_replicates < 1 || n_replicates > kMaxRep) return FAST_EINVAL;
+  if (precision < FAST_FP64 || precision > FAST_FP32_NORECHECK) return FAST_EINVAL;
+  if (reach < FAST_REACH_L2 || reach > FAST_REACH_LINF) return FAST_EINVAL;
+  if ((dev_alloc == nullptr) != (dev_free == nullptr)) return FAST_EINVAL;
+  int dev = 0, ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return FAST_ECUDA;
+  }
+  fast_ctx* c = new fast_ctx();
+  c->n_rep = n_replicates;
+  c->precision = precision;
+  c->reach = reach;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->alloc = dev_alloc;
+  c->release = dev_free;
+  c->user = alloc_user;
+  c->reps.resize(n_replicates);
+  for (int i = 0; i < 5; ++i) c->lanes[i] = kDefaultLanes[i];
+  const int rc = create_impl(c, n_replicates);
+  if (rc != FAST_OK) {
+    fast_destroy(c);
+    return rc;
+  }
+  *out = c;
+  (void)dev;
+  return FAST_OK;
+}
+
+static int create_impl(fast_ctx* c, int32_t n_replicates) {
+  int dev = 0;
+  CUDA_TRY(c, cudaGetDevice(&dev));
+  CUDA_TRY(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+  if (int e = alloc_into(c, &c->d_reps, n_replicates)) return e;
+  if (int e = alloc_into(c, &c->d_ctl, 1)) return e;
+  if (int e = alloc_into(c, &c->d_nslots, n_replicates)) return e;
+  if (int e = alloc_into(c, &c->d_exited, n_replicates)) return e;
+  for (auto& ev : c->ev) CUDA_TRY(c, cudaEventCreate(&ev));
+  CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  c->cur = c->stream;
+  Ctl h{};
+  h.resort_period = c->resort_period;
+  h.barrier_ns_limit = (unsigned long long)c->barrier_ns;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_nslots, 0, 4 * n_replicates, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(c->d_exited, 0, 4 * n_replicates, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return FAST_OK;
+}
+
+int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (!rep_ok(c, r) || !g) return fail(c, FAST_EINVAL, "bad replicate index or NULL grid");
+  if (g->width < 1 || g->height < 1 || (int64_t)g->width * g->height >= ((int64_t)1 << 31))
+    return fail(c, FAST_EINVAL, "grid %d x %d out of range", g->width, g->height);
+  if (!g->cell_type) return fail(c, FAST_EINVAL, "cell_type is NULL");
+  if (g->v_m < 1 || g->v_m > 5) return fail(c, FAST_EINVAL, "v_m = %d not in 1..5", g->v_m);
+  if (!(g->k_S >= 0.0) || !std::isfinite(g->k_S))
+    return fail(c, FAST_EINVAL, "k_S must be finite and >= 0");
+  const double span = g->k_S * g->v_m * kSqrt2;
+  if (c->precision != FAST_FP64 && span * kLog2e > 120.0)
+    return fail(c, FAST_EINVAL, "k_S * v_m * sqrt2 too large for FP32 weights");
+  if (span > 700.0) return fail(c, FAST_EINVAL, "k_S * v_m * sqrt2 too large");
+  const int64_t C = (int64_t)g->width * g->height;
+  int64_t exits = 0;
+  for (int64_t i = 0; i < C; ++i) {
+    if (g->cell_type[i] > 2) return fail(c, FAST_EINVAL, "cell type %d at %lld", g->cell_type[i], (long long)i);
+    exits += g->cell_type[i] == FAST_CELL_EXIT;
+  }
+  if (exits == 0) return fail(c, FAST_EINVAL, "grid has no exit cell");
+
+  std::vector<int32_t> a(C), b(C);
+  exact_floor_field(g->width, g->height, g->cell_type, a.data(), b.data());
+  std::vector<uint32_t> rec(C);
+  RepHost& R = c->reps[r];
+  R.placeable.assign(C, 0);
+  R.seen.assign(C, 0);
+  for (int64_t i = 0; i < C; ++i) {
+    if (a[i] < 0) {
+      rec[i] = 0x7FFFu | (0x7FFFu << 15) | 0x40000000u;
+      continue;
+    }
+    if (a[i] > 0x7FFE || b[i] > 0x7FFE)
+      return fail(c, FAST_EINVAL, "distance to the nearest exit too long at cell %lld", (long long)i);
+    rec[i] = (uint32_t)a[i] | ((uint32_t)b[i] << 15);
+    R.placeable[i] = g->cell_type[i] == FAST_CELL_FREE;
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // (re)allocate the per-cell arrays
+  dfree(c, R.d.rec);
+  dfree(c, R.d.mask);
+  dfree(c, R.d.claim[0]);
+  dfree(c, R.d.claim[1]);
+  R.d.rec = nullptr;
+  R.d.mask = nullptr;
+  R.d.claim[0] = R.d.claim[1] = nullptr;
+  R.W = g->width;
+  R.H = g->height;
+  R.v = g->v_m;
+  R.kS = g->k_S;
+  R.seed = g->seed;
+  R.K = reach_count_host(R.v, c->reach);
+  R.mw = R.K > 64 ? 2 : 1;
+  if (int e = alloc_into(c, &R.d.rec, C)) return e;
+  if (int e = alloc_into(c, &R.d.mask, C * R.mw)) return e;
+  if (int e = alloc_into(c, &R.d.claim[0], C)) return e;
+  if (int e = alloc_into(c, &R.d.claim[1], C)) return e;
+  RepDev& d = R.d;
+  d.W = R.W;
+  d.H = R.H;
+  d.v = R.v;
+  d.reach = c->reach;
+  d.K = R.K;
+  d.mw = R.mw;
+  d.kS = R.kS;
+  d.c32 = (float)(-R.kS * kLog2e);
+  d.margin = margin_of(R.v, R.K, R.kS);
+  d.seed_lo = (uint32_t)R.seed;
+  d.seed_hi = (uint32_t)(R.seed >> 32);
+  CUDA_TRY(c, cudaMemcpyAsync(d.rec, rec.data(), C * 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(d.claim[0], 0xFF, C * 8, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(d.claim[1], 0xFF, C * 8, c->stream));
+  R.grid_set = true;
+  R.placed = false;
+  R.n = 0;
+  const int32_t zero = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots + r, &zero, 4, cudaMemcpyHostToDevice, c->stream));
+  if (int e = upload_reps(c)) return e;
+  LAUNCH_TRY(c, masks_launch(d, c->d_reps + r, C, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->layout_dirty = true;
+  return FAST_OK;
+}
+
+int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, const int32_t* ids,
+                      int32_t start_step) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (!rep_ok(c, r)) return fail(c, FAST_EINVAL, "bad replicate index %d", r);
+  RepHost& R = c->reps[r];
+  if (!R.grid_set) return fail(c, FAST_ESTATE, "grid of replicate %d not set", r);
+  if (n < 0 || n >= (1 << kMaxIdBits)) return fail(c, FAST_EINVAL, "agent count %d out of range", n);
+  if (n > 0 && !cells) return fail(c, FAST_EINVAL, "cells is NULL");
+  if (start_step < 0) return fail(c, FAST_EINVAL, "start_step < 0");
+  const int64_t C = (int64_t)R.W * R.H;
+  // validate cells: placeable and distinct
+  int32_t bad = -1;
+  for (int32_t i = 0; i < n; ++i) {
+    const int32_t cc = cells[i];
+    if (cc < 0 || cc >= C || !R.placeable[cc] || R.seen[cc]) {
+      bad = i;
+      break;
+    }
+    R.seen[cc] = 1;
+  }
+  for (int32_t i = 0; i < n && (bad < 0 || i < bad); ++i) R.seen[cells[i]] = 0;
+  if (bad >= 0)
+    return fail(c, FAST_EINVAL, "agent %d: cell %d is outside, not free, unreachable, an exit or taken",
+                bad, cells[bad]);
+  int32_t id_bound = n;
+  std::vector<int32_t> gen_ids;
+  if (ids) {
+    std::vector<uint8_t> seen_id;
+    int32_t mx = -1;
+    for (int32_t i = 0; i < n; ++i) {
+      if (ids[i] < 0 || ids[i] >= (1 << kMaxIdBits))
+        return fail(c, FAST_EINVAL, "agent %d: id %d not in [0, 2^24)", i, ids[i]);
+      mx = std::max(mx, ids[i]);
+    }
+    seen_id.assign((size_t)mx + 1, 0);
+    for (int32_t i = 0; i < n; ++i) {
+      if (seen_id[ids[i]]) return fail(c, FAST_EINVAL, "duplicate id %d", ids[i]);
+      seen_id[ids[i]] = 1;
+    }
+    id_bound = mx + 1;
+  } else {
+    gen_ids.resize(n);
+    for (int32_t i = 0; i < n; ++i) gen_ids[i] = i;
+    ids = gen_ids.data();
+  }
+
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // clear the previous agents' occupancy marks
+  if (R.placed && R.cap > 0) LAUNCH_TRY(c, clear_occ_launch(c->d_reps + r, c->d_nslots, r, R.cap, c->stream));
+  if (n > R.cap || !R.placed) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int32_t* arrs[] = {R.d.id, R.d.cell, R.d.desired, R.d.id2, R.d.cell2};
+    for (auto p : arrs) dfree(c, p);
+    dfree(c, R.d.prio);
+    dfree(c, R.d.mvinfo);
+    const int32_t cap = std::max(n, std::max(R.cap, 1));
+    if (int e = alloc_into(c, &R.d.id, cap)) return e;
+    if (int e = alloc_into(c, &R.d.cell, cap)) return e;
+    if (int e = alloc_into(c, &R.d.desired, cap)) return e;
+    if (int e = alloc_into(c, &R.d.id2, cap)) return e;
+    if (int e = alloc_into(c, &R.d.cell2, cap)) return e;
+    if (int e = alloc_into(c, &R.d.prio, cap)) return e;
+    if (int e = alloc_into(c, &R.d.mvinfo, cap)) return e;
+    R.cap = cap;
+    R.d.cap = cap;
+    c->layout_dirty = true;
+  }
+  R.placed = true;
+  R.n = n;
+  R.id_bound = id_bound;
+  CUDA_TRY(c, cudaMemsetAsync(R.d.cell, 0xFF, (size_t)R.cap * 4, c->stream));
+  if (n > 0) {
+    CUDA_TRY(c, cudaMemcpyAsync(R.d.cell2, cells, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(R.d.id2, ids, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+  }
+  if (c->layout_dirty) {
+    if (int e = rebuild_layout(c)) return e;
+  }
+  LAUNCH_TRY(c, place_launch(c->d_reps + r, R.d.cell2, R.d.id2, n, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots + r, &n, 4, cudaMemcpyHostToDevice, c->stream));
+  const int32_t zero = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_exited + r, &zero, 4, cudaMemcpyHostToDevice, c->stream));
+  // step index and per-step counters
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->t, &start_step, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->dig_count, &zero, 4, cudaMemcpyHostToDevice, c->stream));
+  const StepArgs a = args_of(c);
+  LAUNCH_TRY(c, step_begin_launch(a, c->stream));
+  // initial Morton order
+  const Chunks all = all_chunks(c);
+  LAUNCH_TRY(c, resort_launch(a, all, plan_grid(c, all.n), true, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->t_host = start_step;
+  c->steps_since_place = 0;
+  return FAST_OK;
+}
+
+int fast_step(fast_ctx* c, int32_t n_steps) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (n_steps < 0) return fail(c, FAST_EINVAL, "n_steps < 0");
+  bool any = false;
+  for (auto& R : c->reps) any = any || R.placed;
+  if (!any) return fail(c, FAST_ESTATE, "no agents placed");
+  if (c->layout_dirty)
+    if (int e = rebuild_layout(c)) return e;
+  if (c->digests && c->steps_since_place + n_steps > c->dig_cap) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int32_t want = (int32_t)std::max<int64_t>(1024, 2 * (c->steps_since_place + n_steps));
+    unsigned long long *dc = nullptr, *dd = nullptr;
+    if (int e = alloc_into(c, &dc, (size_t)want * c->n_rep)) return e;
+    if (int e = alloc_into(c, &dd, (size_t)want * c->n_rep)) return e;
+    CUDA_TRY(c, cudaMemsetAsync(dc, 0, (size_t)want * c->n_rep * 8, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(dd, 0, (size_t)want * c->n_rep * 8, c->stream));
+    if (c->d_dig_cell) {
+      CUDA_TRY(c, cudaMemcpyAsync(dc, c->d_dig_cell, (size_t)c->dig_cap * c->n_rep * 8,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+      CUDA_TRY(c, cudaMemcpyAsync(dd, c->d_dig_des, (size_t)c->dig_cap * c->n_rep * 8,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    dfree(c, c->d_dig_cell);
+    dfree(c, c->d_dig_des);
+    c->d_dig_cell = dc;
+    c->d_dig_des = dd;
+    c->dig_cap = want;
+    drop_graphs(c);
+  }
+  for (int32_t i = 0; i < n_steps; ++i) {
+    const bool resort = c->resort_period > 0 && ((c->t_host + 1) % c->resort_period == 0);
+    const int which = resort ? 1 : 0;
+    if (c->use_graph && c->graph_state[which] == 0) {
+      if (int e = build_graph(c, which)) return e;
+    }
+    if (c->use_graph && c->graph_state[which] == 1) {
+      CUDA_TRY(c, cudaGraphLaunch(c->graph[which], c->stream));
+      c->launches += c->launches_per_graph[which];
+    } else {
+      if (int e = enqueue_step(c, resort)) return e;
+    }
+    c->t_host += 1;
+    c->steps_since_place += 1;
+  }
+  c->ran_step = c->ran_step || n_steps > 0;
+  return FAST_OK;
+}
+
+int fast_plan_only(fast_ctx* c, int32_t n) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  bool any = false;
+  for (auto& R : c->reps) any = any || R.placed;
+  if (!any) return fail(c, FAST_ESTATE, "no agents placed");
+  if (c->layout_dirty)
+    if (int e = rebuild_layout(c)) return e;
+  const StepArgs a = args_of(c);
+  for (int32_t i = 0; i < n; ++i) {
+    LAUNCH_TRY(c, step_begin_launch(a, c->stream));
+    if (int e = enqueue_plan(c, a, false, false)) return e;
+  }
+  return FAST_OK;
+}
+
+int fast_readback(fast_ctx* c, int32_t r, int32_t id_bound, int32_t* cells_by_id,
+                  int32_t* desired_by_id, fast_stats* stats) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (!rep_ok(c, r) || id_bound < 0) return fail(c, FAST_EINVAL, "bad replicate or id_bound");
+  RepHost& R = c->reps[r];
+  if (int e = check_device_error(c)) return e;
+  if (id_bound > 0 && (cells_by_id || desired_by_id)) {
+    if (id_bound * 2 > c->gather_cap) {
+      dfree(c, c->d_gather);
+      c->d_gather = nullptr;
+      if (int e = alloc_into(c, &c->d_gather, (size_t)id_bound * 2)) return e;
+      c->gather_cap = id_bound * 2;
+    }
+    CUDA_TRY(c, cudaMemsetAsync(c->d_gather, 0xFF, (size_t)id_bound * 8, c->stream));
+    if (R.placed)
+      LAUNCH_TRY(c, gather_by_id_launch(c->d_reps + r, c->d_nslots, r, R.cap, c->d_gather,
+                                        c->d_gather + id_bound, id_bound, c->stream));
+    if (cells_by_id)
+      CUDA_TRY(c, cudaMemcpyAsync(cells_by_id, c->d_gather, (size_t)id_bound * 4,
+                                  cudaMemcpyDeviceToHost, c->stream));
+    if (desired_by_id)
+      CUDA_TRY(c, cudaMemcpyAsync(desired_by_id, c->d_gather + id_bound, (size_t)id_bound * 4,
+                                  cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  }
+  if (stats) {
+    Ctl h{};
+    int32_t ex = 0;
+    CUDA_TRY(c, cudaMemcpy(&h, c->d_ctl, sizeof h, cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(&ex, c->d_exited + r, 4, cudaMemcpyDeviceToHost));
+    stats->step = h.t;
+    stats->steps_run = c->steps_since_place;
+    stats->exited = ex;
+    stats->alive = R.n - ex;
+    stats->agent_steps = (int64_t)h.agent_steps;
+    stats->rechecked = (int64_t)h.rechecked_total;
+    stats->move_rounds = (int64_t)h.rounds_total;
+    stats->max_rounds = h.rounds_max;
+    stats->last_rounds = h.rounds_last;
+    stats->kernel_launches = c->launches;
+  }
+  return FAST_OK;
+}
+
+int fast_get_digests(fast_ctx* c, int32_t r, int32_t max_steps, uint64_t* cell_digest,
+                     uint64_t* desired_digest) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (!rep_ok(c, r) || max_steps < 0) return fail(c, FAST_EINVAL, "bad arguments");
+  if (int e = check_device_error(c)) return e;
+  int32_t cnt = 0;
+  CUDA_TRY(c, cudaMemcpy(&cnt, &c->d_ctl->dig_count, 4, cudaMemcpyDeviceToHost));
+  cnt = std::min(cnt, std::min(max_steps, c->dig_cap));
+  if (cnt <= 0 || !c->d_dig_cell) return 0;
+  std::vector<unsigned long long> a((size_t)cnt * c->n_rep), b((size_t)cnt * c->n_rep);
+  CUDA_TRY(c, cudaMemcpy(a.data(), c->d_dig_cell, a.size() * 8, cudaMemcpyDeviceToHost));
+  CUDA_TRY(c, cudaMemcpy(b.data(), c->d_dig_des, b.size() * 8, cudaMemcpyDeviceToHost));
+  for (int32_t i = 0; i < cnt; ++i) {
+    if (cell_digest) cell_digest[i] = a[(size_t)i * c->n_rep + r];
+    if (desired_digest) desired_digest[i] = b[(size_t)i * c->n_rep + r];
+  }
+  return cnt;
+}
+
+int fast_phase_times(fast_ctx* c, float* ms4) {
+  if (!c || !ms4) return FAST_EINVAL;
+  if (!c->ran_step) return fail(c, FAST_ESTATE, "no step has run");
+  CUDA_TRY(c, cudaEventSynchronize(c->ev[4]));
+  for (int i = 0; i < 4; ++i) CUDA_TRY(c, cudaEventElapsedTime(&ms4[i], c->ev[i], c->ev[i + 1]));
+  return FAST_OK;
+}
+
+int fast_precision_report_run(fast_ctx* c, fast_precision_report* out) {
+  if (!c || !out) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (c->precision == FAST_FP64) return fail(c, FAST_ESTATE, "context plans in FP64");
+  bool any = false;
+  for (auto& R : c->reps) any = any || R.placed;
+  if (!any) return fail(c, FAST_ESTATE, "no agents placed");
+  if (c->layout_dirty)
+    if (int e = rebuild_layout(c)) return e;
+  std::vector<int64_t> base(c->n_rep, 0);
+  int64_t total = 0;
+  double margin = 0.0;
+  for (int r = 0; r < c->n_rep; ++r) {
+    base[r] = total;
+    if (c->reps[r].placed) {
+      total += c->reps[r].cap;
+      margin = std::max(margin, (double)c->reps[r].d.margin);
+    }
+  }
+  float* p32 = nullptr;
+  int32_t* ch32 = nullptr;
+  uint8_t* fl = nullptr;
+  int64_t* db = nullptr;
+  if (int e = alloc_into(c, &p32, (size_t)total * kMaxK)) return e;
+  if (int e = alloc_into(c, &ch32, (size_t)total)) return e;
+  if (int e = alloc_into(c, &fl, (size_t)total)) return e;
+  if (int e = alloc_into(c, &db, (size_t)c->n_rep)) return e;
+  CUDA_TRY(c, cudaMemcpyAsync(db, base.data(), 8 * c->n_rep, cudaMemcpyHostToDevice, c->stream));
+  const unsigned long long z[3] = {0, 0, 0};
+  const unsigned int zi = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->flips, z, 24, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->max_dp_bits, &zi, 4, cudaMemcpyHostToDevice, c->stream));
+  StepArgs a = args_of(c);
+  a.diag_p32 = p32;
+  a.diag_choice32 = ch32;
+  a.diag_flag = fl;
+  a.diag_base = db;
+  if (int e = enqueue_plan(c, a, true, false)) return e;
+  for (auto& g : c->groups) {
+    Chunks ch{g.d_rep, g.d_begin, g.n};
+    LAUNCH_TRY(c, plan_diag_compare_launch(a, g.v, c->reach, ch, plan_grid(c, g.n), c->stream));
+  }
+  Ctl h{};
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  CUDA_TRY(c, cudaMemcpy(&h, c->d_ctl, sizeof h, cudaMemcpyDeviceToHost));
+  int64_t agents = 0;
+  for (int r = 0; r < c->n_rep; ++r) {
+    if (!c->reps[r].placed) continue;
+    int32_t ns = 0, ex = 0;
+    CUDA_TRY(c, cudaMemcpy(&ns, c->d_nslots + r, 4, cudaMemcpyDeviceToHost));
+    CUDA_TRY(c, cudaMemcpy(&ex, c->d_exited + r, 4, cudaMemcpyDeviceToHost));
+    agents += c->reps[r].n - ex;
+  }
+  dfree(c, p32);
+  dfree(c, ch32);
+  dfree(c, fl);
+  dfree(c, db);
+  out->agents = agents;
+  out->flagged = (int64_t)h.flagged;
+  out->flips = (int64_t)h.flips;
+  out->flips_unflagged = (int64_t)h.flips_unflagged;
+  float mdp;
+  std::memcpy(&mdp, &h.max_dp_bits, 4);
+  out->max_abs_dp = mdp;
+  out->margin = margin;
+  return FAST_OK;
+}
+
+int fast_reach_union(fast_ctx* c, int32_t r, int64_t* cells) {
+  if (!c || !cells) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (!rep_ok(c, r) || !c->reps[r].placed) return fail(c, FAST_ESTATE, "replicate not placed");
+  if (c->layout_dirty)
+    if (int e = rebuild_layout(c)) return e;
+  RepHost& R = c->reps[r];
+  const int64_t words = ((int64_t)R.W * R.H + 31) / 32;
+  uint32_t* bm = nullptr;
+  unsigned long long* cnt = nullptr;
+  if (int e = alloc_into(c, &bm, (size_t)words)) return e;
+  if (int e = alloc_into(c, &cnt, 1)) return e;
+  LAUNCH_TRY(c, union_count_launch(c->d_reps + r, c->d_nslots, r, R.cap, R.v, c->reach, R.W, R.H,
+                                   bm, cnt, c->stream));
+  unsigned long long h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  dfree(c, bm);
+  dfree(c, cnt);
+  *cells = (int64_t)h;
+  return FAST_OK;
+}
+
+int fast_set_option(fast_ctx* c, int32_t option, int64_t value) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  switch (option) {
+    case FAST_OPT_RESORT_PERIOD:
+      if (value < 0) return fail(c, FAST_EINVAL, "resort period < 0");
+      c->resort_period = (int)value;
+      break;
+    case FAST_OPT_DIGESTS:
+      c->digests = value != 0;
+      break;
+    case FAST_OPT_BARRIER_NS: {
+      if (value < 1000) return fail(c, FAST_EINVAL, "barrier limit below 1 us");
+      c->barrier_ns = value;
+      const unsigned long long v = (unsigned long long)value;
+      CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->barrier_ns_limit, &v, 8, cudaMemcpyHostToDevice,
+                                  c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      break;
+    }
+    case FAST_OPT_USE_GRAPH:
+      c->use_graph = value != 0;
+      break;
+    case FAST_OPT_MOVE_BLOCKS:
+      if (value < 0) return fail(c, FAST_EINVAL, "move blocks < 0");
+      c->move_blocks = (int)value;
+      break;
+    case FAST_OPT_TILE_SHIFT:
+      if (value < 0 || value > 10) return fail(c, FAST_EINVAL, "tile shift not in 0..10");
+      c->tile_shift = (int)value;
+      c->layout_dirty = true;
+      break;
+    default:
+      if (option >= FAST_OPT_LANES_V1 && option < FAST_OPT_LANES_V1 + 5) {
+        if (value != 1 && value != 2 && value != 4 && value != 8)
+          return fail(c, FAST_EINVAL, "lanes must be 1, 2, 4 or 8");
+        c->lanes[option - FAST_OPT_LANES_V1] = (int)value;
+        break;
+      }
+      return fail(c, FAST_EINVAL, "unknown option %d", option);
+  }
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  return FAST_OK;
+}
+
+const char* fast_last_error(const fast_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+void fast_destroy(fast_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  cudaGetLastError();
+  drop_graphs(c);
+  for (auto& ev : c->ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  std::vector<void*> ptrs;
+  for (auto& kv : c->live) ptrs.push_back(kv.first);
+  for (void* p : ptrs) dfree(c, p);
+  delete c;
+}
+
+// ---- self tests ------------------------------------------------------------
+int fast_selftest_exp64(const double* x, double* y, int64_t n) {
+  if (n < 0 || (n > 0 && (!x || !y))) return FAST_EINVAL;
+  if (n == 0) return FAST_OK;
+  double *dx = nullptr, *dy = nullptr;
+  if (cudaMalloc(&dx, n * 8) != cudaSuccess) return FAST_ENOMEM;
+  if (cudaMalloc(&dy, n * 8) != cudaSuccess) {
+    cudaFree(dx);
+    return FAST_ENOMEM;
+  }
+  int rc = FAST_OK;
+  if (cudaMemcpy(dx, x, n * 8, cudaMemcpyHostToDevice) != cudaSuccess) rc = FAST_ECUDA;
+  if (rc == FAST_OK) {
+    test_exp64_launch(dx, dy, n, 0);
+    if (cudaGetLastError() != cudaSuccess) rc = FAST_ECUDA;
+  }
+  if (rc == FAST_OK && cudaMemcpy(y, dy, n * 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = FAST_ECUDA;
+  cudaFree(dx);
+  cudaFree(dy);
+  return rc;
+}
+
+int fast_selftest_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n) {
+  if (n < 0 || (n > 0 && (!ctr || !key || !out))) return FAST_EINVAL;
+  if (n == 0) return FAST_OK;
+  uint32_t *dc = nullptr, *dk = nullptr, *dout = nullptr;
+  if (cudaMalloc(&dc, n * 16) != cudaSuccess) return FAST_ENOMEM;
+  if (cudaMalloc(&dk, n * 8) != cudaSuccess || cudaMalloc(&dout, n * 16) != cudaSuccess) {
+    cudaFree(dc);
+    cudaFree(dk);
+    return FAST_ENOMEM;
+  }
+  int rc = FAST_OK;
+  if (cudaMemcpy(dc, ctr, n * 16, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dk, key, n * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+    rc = FAST_ECUDA;
+  if (rc == FAST_OK) {
+    test_philox_launch(dc, dk, dout, n, 0);
+    if (cudaGetLastError() != cudaSuccess) rc = FAST_ECUDA;
+  }
+  if (rc == FAST_OK && cudaMemcpy(out, dout, n * 16, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = FAST_ECUDA;
+  cudaFree(dc);
+  cudaFree(dk);
+  cudaFree(dout);
+  return rc;
+}
+
+int fast_selftest_ex2(float lo, float hi, double* max_rel_err) {
+  if (!max_rel_err || !(lo <= hi)) return FAST_EINVAL;
+  unsigned long long* d = nullptr;
+  if (cudaMalloc(&d, 8) != cudaSuccess) return FAST_ENOMEM;
+  int rc = FAST_OK;
+  if (cudaMemset(d, 0, 8) != cudaSuccess) rc = FAST_ECUDA;
+  // walk non-negative and negative floats separately (bit order = value order
+  // for non-negative floats, reversed for negative ones)
+  if (rc == FAST_OK && hi >= 0.f) test_ex2_launch(lo > 0.f ? lo : 0.f, hi, d, 0);
+  if (rc == FAST_OK && lo < 0.f) test_ex2_launch(-0.0f, lo, d, 0);
+  if (rc == FAST_OK && cudaGetLastError() != cudaSuccess) rc = FAST_ECUDA;
+  unsigned long long h = 0;
+  if (rc == FAST_OK && cudaMemcpy(&h, d, 8, cudaMemcpyDeviceToHost) != cudaSuccess) rc = FAST_ECUDA;
+  cudaFree(d);
+  double v;
+  std::memcpy(&v, &h, 8);
+  *max_rel_err = v;
+  return rc;
+}
+
+int fast_selftest_barrier_timeout(int64_t limit_ns) {
+  if (limit_ns < 1000 || limit_ns > 10000000000ll) return FAST_EINVAL;
+  Ctl* d = nullptr;
+  if (cudaMalloc(&d, sizeof(Ctl)) != cudaSuccess) return FAST_ENOMEM;
+  Ctl h{};
+  h.barrier_ns_limit = (unsigned long long)limit_ns;
+  int rc = FAST_OK;
+  if (cudaMemcpy(d, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess) rc = FAST_ECUDA;
+  if (rc == FAST_OK && test_barrier_timeout_launch(d, 2, 0) != 0) rc = FAST_ECUDA;
+  if (rc == FAST_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FAST_ECUDA;
+  if (rc == FAST_OK && cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = FAST_ECUDA;
+  cudaFree(d);
+  if (rc != FAST_OK) return rc;
+  return h.err == kDevErrTimeout ? FAST_ETIMEOUT : FAST_OK;
+}
+
+}  // extern "C"

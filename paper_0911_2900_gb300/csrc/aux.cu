@@ -1,0 +1,371 @@
+// aux.cu -- set-up and bookkeeping kernels: line-of-sight masks, agent
+// placement, Morton re-sort with compaction of agents that left, digests,
+// read-back gathers, the reach-union counter used for byte accounting, and
+// the kernels behind the library's self-test entry points.
+#include "fast_device.cuh"
+
+namespace fastgb {
+
+// ---------------------------------------------------------------------------
+// Line-of-sight mask of every cell: bit k set when the k-th reach offset lands
+// inside the grid and its straight path crosses no wall (nor any cell that no
+// exit can be reached from).  Static for the lifetime of the grid.
+__global__ void k_masks(const RepDev* rp, int64_t cells) {
+  const RepDev R = *rp;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cells;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long m[2] = {0ull, 0ull};
+    if (!rec_sentinel(R.rec[c])) {
+      const int x0 = (int)(c % R.W), y0 = (int)(c / R.W);
+      int k = 0;
+      for (int dy = -R.v; dy <= R.v; ++dy)
+        for (int dx = -R.v; dx <= R.v; ++dx) {
+          if (!reach_in(dx, dy, R.v, R.reach)) continue;
+          const int tx = x0 + dx, ty = y0 + dy;
+          bool ok = tx >= 0 && tx < R.W && ty >= 0 && ty < R.H;
+          const int L = max(abs(dx), abs(dy));
+          for (int s = 1; ok && s <= L; ++s) {
+            const int px = x0 + div_half_away(s * dx, L), py = y0 + div_half_away(s * dy, L);
+            ok = !rec_sentinel(R.rec[(int64_t)py * R.W + px]);
+          }
+          if (ok) m[k >> 6] |= 1ull << (k & 63);
+          ++k;
+        }
+    }
+    R.mask[c * R.mw] = m[0];
+    if (R.mw > 1) R.mask[c * R.mw + 1] = m[1];
+  }
+}
+
+int masks_launch(const RepDev& h, RepDev* d, int64_t cells, cudaStream_t s) {
+  (void)h;
+  const int64_t blocks = (cells + 255) / 256;
+  k_masks<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(d, cells);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Placement: clear the previous agents' marks, then write the new agents.
+__global__ void k_clear_occ(RepDev* rp, const int32_t* n_slots, int rep, int cap) {
+  const RepDev& R = *rp;
+  const int n = min(n_slots[rep], cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = R.cell[i];
+    if (c >= 0) R.rec[c] &= ~(REC_OCC | REC_STA);
+    R.cell[i] = -1;
+  }
+}
+
+int clear_occ_launch(RepDev* d, const int32_t* n_slots, int rep, int cap, cudaStream_t s) {
+  k_clear_occ<<<(cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, 256, 0, s>>>(d, n_slots, rep, cap);
+  return 0;
+}
+
+__global__ void k_place(RepDev* rp, const int32_t* cells, const int32_t* ids, int n) {
+  const RepDev& R = *rp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = cells[i];
+    R.cell[i] = c;
+    R.id[i] = ids[i];
+    R.desired[i] = c;
+    R.rec[c] = (R.rec[c] & ~REC_STA) | REC_OCC;
+  }
+}
+
+int place_launch(RepDev* d, const int32_t* cells, const int32_t* ids, int n, cudaStream_t s) {
+  if (n <= 0) return 0;
+  k_place<<<(n + 255) / 256, 256, 0, s>>>(d, cells, ids, n);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Morton re-sort.  Buckets are 2^tile_shift square tiles numbered along the
+// Z-order curve inside each replicate; a counting sort by bucket keeps agents
+// that are close on the grid close in memory and drops agents that left.
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+  x &= 0xFFFFu;
+  x = (x | (x << 8)) & 0x00FF00FFu;
+  x = (x | (x << 4)) & 0x0F0F0F0Fu;
+  x = (x | (x << 2)) & 0x33333333u;
+  x = (x | (x << 1)) & 0x55555555u;
+  return x;
+}
+
+__device__ __forceinline__ int bucket_of(const RepDev& R, int cell) {
+  const int x = cell % R.W, y = cell / R.W;
+  const uint32_t m = spread16((uint32_t)(x >> R.tile_shift)) |
+                     (spread16((uint32_t)(y >> R.tile_shift)) << 1);
+  return R.bucket_base + (int)m;
+}
+
+__global__ void k_bucket_zero(StepArgs a) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= a.n_buckets;
+       i += gridDim.x * blockDim.x)
+    a.bucket_count[i] = 0u;
+}
+
+__global__ void k_bucket_count(StepArgs a, Chunks ch) {
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const RepDev& R = a.reps[rep];
+    const int slot = ch.begin[c] + threadIdx.x;
+    if (slot >= min(ch.begin[c] + kChunk, a.n_slots[rep])) continue;
+    const int cell = R.cell[slot];
+    if (cell >= 0) atomicAdd(&a.bucket_count[bucket_of(R, cell)], 1u);
+  }
+}
+
+// One block: exclusive scan of the bucket counts (in place), then the number
+// of agents of each replicate (= its new slot count).
+__global__ void __launch_bounds__(1024) k_bucket_scan(StepArgs a) {
+  __shared__ uint32_t s_part[1024];
+  const int n = a.n_buckets;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+  uint32_t sum = 0;
+  for (int i = lo; i < hi; ++i) sum += a.bucket_count[i];
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const uint32_t v = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    s_part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  uint32_t run = s_part[threadIdx.x] - sum;
+  for (int i = lo; i < hi; ++i) {
+    const uint32_t v = a.bucket_count[i];
+    a.bucket_count[i] = run;
+    run += v;
+  }
+  __syncthreads();
+  if (threadIdx.x == blockDim.x - 1) a.bucket_count[n] = run;
+  __syncthreads();
+  for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) {
+    const RepDev& R = a.reps[r];
+    const uint32_t b0 = a.bucket_count[R.bucket_base];
+    const uint32_t b1 = a.bucket_count[R.bucket_base + R.bucket_span];
+    // per replicate: its first offset (the scatter subtracts it) and its new
+    // agent count (the copy and the commit use it)
+    a.bucket_count[a.n_buckets + 1 + 2 * r] = b0;
+    a.bucket_count[a.n_buckets + 2 + 2 * r] = b1 - b0;
+  }
+}
+
+__global__ void k_bucket_scatter(StepArgs a, Chunks ch) {
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const RepDev& R = a.reps[rep];
+    const int slot = ch.begin[c] + threadIdx.x;
+    if (slot >= min(ch.begin[c] + kChunk, a.n_slots[rep])) continue;
+    const int cell = R.cell[slot];
+    if (cell < 0) continue;
+    const uint32_t pos = atomicAdd(&a.bucket_count[bucket_of(R, cell)], 1u) -
+                         a.bucket_count[a.n_buckets + 1 + 2 * rep];
+    R.id2[pos] = R.id[slot];
+    R.cell2[pos] = cell;
+    R.mvinfo[pos] = (uint32_t)R.desired[slot];  // movement scratch, free until the next step
+  }
+}
+
+__global__ void k_bucket_copy(StepArgs a, Chunks ch) {
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const RepDev& R = a.reps[rep];
+    const int n_new = (int)a.bucket_count[a.n_buckets + 2 + 2 * rep];
+    const int slot = ch.begin[c] + threadIdx.x;
+    if (slot >= min(ch.begin[c] + kChunk, a.n_slots[rep])) continue;
+    if (slot < n_new) {
+      R.id[slot] = R.id2[slot];
+      R.cell[slot] = R.cell2[slot];
+      R.desired[slot] = (int32_t)R.mvinfo[slot];
+    } else {
+      R.cell[slot] = -1;
+    }
+  }
+}
+
+__global__ void k_bucket_commit(StepArgs a) {
+  for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x)
+    a.n_slots[r] = (int)a.bucket_count[a.n_buckets + 2 + 2 * r];
+}
+
+int resort_launch(const StepArgs& a, const Chunks& ch, int grid, bool force, cudaStream_t s) {
+  (void)force;
+  if (ch.n <= 0) return 0;
+  k_bucket_zero<<<256, 256, 0, s>>>(a);
+  k_bucket_count<<<grid, kChunk, 0, s>>>(a, ch);
+  k_bucket_scan<<<1, 1024, 0, s>>>(a);
+  k_bucket_scatter<<<grid, kChunk, 0, s>>>(a, ch);
+  k_bucket_copy<<<grid, kChunk, 0, s>>>(a, ch);
+  k_bucket_commit<<<1, 256, 0, s>>>(a);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Digests (splitmix64 output function of (id << 32 | value), summed).
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void k_digest(StepArgs a, Chunks ch, int which) {
+  const int idx = a.ctl->dig_count;
+  if (idx >= a.dig_cap) return;
+  unsigned long long* out = (which == 0 ? a.dig_cell : a.dig_des) + (int64_t)idx * a.n_rep;
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const RepDev& R = a.reps[rep];
+    const int slot = ch.begin[c] + threadIdx.x;
+    if (slot >= min(ch.begin[c] + kChunk, a.n_slots[rep])) continue;
+    const int cell = R.cell[slot];
+    if (cell < 0) continue;
+    const int v = which == 0 ? cell : R.desired[slot];
+    atomicAdd(&out[rep], mix64(((unsigned long long)(uint32_t)R.id[slot] << 32) | (uint32_t)v));
+  }
+}
+
+__global__ void k_digest_advance(StepArgs a) {
+  if (threadIdx.x == 0) a.ctl->dig_count += 1;
+}
+
+int digest_des_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s) {
+  if (ch.n <= 0) return 0;
+  k_digest<<<grid, kChunk, 0, s>>>(a, ch, 1);
+  return 0;
+}
+
+int digest_cell_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s) {
+  if (ch.n > 0) k_digest<<<grid, kChunk, 0, s>>>(a, ch, 0);
+  k_digest_advance<<<1, 32, 0, s>>>(a);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_gather_by_id(const RepDev* rp, const int32_t* n_slots, int rep, int cap,
+                               int32_t* out_cell, int32_t* out_desired, int32_t bound) {
+  const RepDev& R = *rp;
+  const int n = min(n_slots[rep], cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = R.cell[i];
+    if (c < 0) continue;
+    const int id = R.id[i];
+    if (id < 0 || id >= bound) continue;
+    if (out_cell) out_cell[id] = c;
+    if (out_desired) out_desired[id] = R.desired[i];
+  }
+}
+
+int gather_by_id_launch(const RepDev* d, const int32_t* n_slots, int rep, int cap,
+                        int32_t* out_cell, int32_t* out_desired, int32_t bound, cudaStream_t s) {
+  const int blocks = cap > 0 ? (cap + 255) / 256 : 1;
+  k_gather_by_id<<<blocks, 256, 0, s>>>(d, n_slots, rep, cap, out_cell, out_desired, bound);
+  return 0;
+}
+
+// Number of distinct cells whose record one planning pass reads: the own cell
+// of every agent and every in-grid, line-of-sight offset of its reach set.
+__global__ void k_union_mark(const RepDev* rp, const int32_t* n_slots, int rep, int cap,
+                             uint32_t* bitmap) {
+  const RepDev& R = *rp;
+  const int n = min(n_slots[rep], cap);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int c = R.cell[i];
+    if (c < 0) continue;
+    const unsigned long long m0 = R.mask[(size_t)c * R.mw];
+    const unsigned long long m1 = R.mw > 1 ? R.mask[(size_t)c * R.mw + 1] : 0ull;
+    int k = 0;
+    for (int dy = -R.v; dy <= R.v; ++dy)
+      for (int dx = -R.v; dx <= R.v; ++dx) {
+        if (!reach_in(dx, dy, R.v, R.reach)) continue;
+        const bool bit = k < 64 ? ((m0 >> k) & 1ull) : ((m1 >> (k - 64)) & 1ull);
+        if (bit) {
+          const int64_t cc = (int64_t)c + (int64_t)dy * R.W + dx;
+          atomicOr(&bitmap[cc >> 5], 1u << (cc & 31));
+        }
+        ++k;
+      }
+  }
+}
+
+__global__ void k_union_pop(const uint32_t* bitmap, int64_t words, unsigned long long* out) {
+  unsigned long long s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < words;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += __popc(bitmap[i]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(out, s);
+}
+
+int union_count_launch(const RepDev* d, const int32_t* n_slots, int rep, int cap, int v,
+                       int reach, int W, int H, uint32_t* bitmap, unsigned long long* out,
+                       cudaStream_t s) {
+  (void)v;
+  (void)reach;
+  const int64_t words = ((int64_t)W * H + 31) / 32;
+  cudaMemsetAsync(bitmap, 0, (size_t)words * 4, s);
+  cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  k_union_mark<<<cap > 0 ? (cap + 255) / 256 : 1, 256, 0, s>>>(d, n_slots, rep, cap, bitmap);
+  k_union_pop<<<1024, 256, 0, s>>>(bitmap, words, out);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Self-test kernels.
+__global__ void k_test_exp64(const double* x, double* y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = exp64(x[i]);
+}
+
+int test_exp64_launch(const double* x, double* y, int64_t n, cudaStream_t s) {
+  k_test_exp64<<<1024, 256, 0, s>>>(x, y, n);
+  return 0;
+}
+
+__global__ void k_test_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const U4 r = philox10(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], key[2 * i],
+                          key[2 * i + 1]);
+    out[4 * i] = r.x;
+    out[4 * i + 1] = r.y;
+    out[4 * i + 2] = r.z;
+    out[4 * i + 3] = r.w;
+  }
+}
+
+int test_philox_launch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
+                       cudaStream_t s) {
+  k_test_philox<<<256, 256, 0, s>>>(ctr, key, out, n);
+  return 0;
+}
+
+// Largest relative error of ex2.approx.ftz.f32 over every float in [lo, hi],
+// against the FP64 exponential of this file (exp64(y * ln 2)), as float bits.
+__global__ void k_test_ex2(float lo, float hi, unsigned long long* out) {
+  const int32_t blo = __float_as_int(lo), bhi = __float_as_int(hi);
+  double worst = 0.0;
+  // walk the float bit patterns between lo and hi (both of one sign handled
+  // by the host splitting the range at zero)
+  const int64_t n = (int64_t)bhi - blo + 1;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float y = __int_as_float((int32_t)(blo + i));
+    const float e = ex2_approx(y);
+    const double ref = exp64(__dmul_rn((double)y, 0x1.62e42fefa39efp-1));
+    const double rel = fabs(((double)e - ref) / ref);
+    worst = fmax(worst, rel);
+  }
+  for (int o = 16; o > 0; o >>= 1) worst = fmax(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(worst));
+}
+
+int test_ex2_launch(float lo, float hi, unsigned long long* out, cudaStream_t s) {
+  k_test_ex2<<<1024, 256, 0, s>>>(lo, hi, out);
+  return 0;
+}
+
+}  // namespace fastgb

@@ -1,0 +1,128 @@
+// fast_internal.h -- declarations shared by the host API (api.cpp) and the
+// CUDA translation units of libfastgb.  Not part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fastgb {
+
+enum { REACH_L2 = 0, REACH_L2P = 1, REACH_LINF = 2 };
+enum { PREC_FP64 = 0, PREC_FP32_RECHECK = 1, PREC_FP32_NORECHECK = 2 };
+
+constexpr int kMaxRep = 256;        // replicates per context (8-bit field in work refs)
+constexpr int kMaxIdBits = 24;      // agent ids < 2^24 (movement priority layout)
+constexpr int kChunk = 256;         // agents per work chunk
+constexpr int kMaxK = 121;          // largest reach set (L-infinity, v_m = 5)
+constexpr int kDevErrTimeout = 5;   // device error: a bounded wait gave up
+constexpr int kDevErrRounds = 6;    // device error: movement rounds exceeded the bound
+
+// Per-replicate descriptor, resident in device memory.
+struct RepDev {
+  int32_t W, H, v, reach, K, mw;    // mw: 64-bit mask words per cell (1 or 2)
+  int32_t cap;                      // agent slots allocated
+  int32_t tile_shift;               // Morton buckets are 2^tile_shift square tiles
+  int32_t tiles_x, tiles_y;         // tiles per row / column
+  int32_t bucket_base, bucket_span; // this replicate's range in the bucket arrays
+  float c32;                        // fl32(-k_S * log2(e))
+  float margin;                     // relative margin M of the FP32 decision
+  double kS;
+  uint32_t seed_lo, seed_hi;
+  uint32_t* rec;                    // [W*H] cell records
+  unsigned long long* mask;         // [W*H*mw] line-of-sight masks
+  unsigned long long* claim[2];     // [W*H] movement claims (ping-pong)
+  int32_t* id;                      // [cap]
+  int32_t* cell;                    // [cap]  -1: slot empty / agent left
+  int32_t* desired;                 // [cap]
+  int32_t* id2;                     // [cap]  re-sort buffers
+  int32_t* cell2;                   // [cap]
+  unsigned long long* prio;         // [cap]  movement priority this step
+  uint32_t* mvinfo;                 // [cap]  footprint length | flags
+};
+
+// Step-wide control block, resident in device memory.
+struct Ctl {
+  int32_t t;                  // step index of the next step
+  int32_t err;                // first device error (0 = none)
+  uint32_t q_count;           // FP64 re-check queue length, this step
+  uint32_t act_count[3];      // movement list lengths (ping-pong + initial)
+  uint32_t bar_count;         // grid barrier arrivals
+  uint32_t bar_gen;           // grid barrier generation
+  int32_t rounds_last;        // movement rounds of the last step
+  int32_t rounds_max;
+  int32_t resort_period;      // re-sort agents every this many steps (0: never)
+  int32_t digests_on;
+  int32_t dig_count;          // digests written
+  int32_t pad0;
+  unsigned long long rounds_total;
+  unsigned long long rechecked_total;
+  unsigned long long agent_steps;
+  unsigned long long barrier_ns_limit;
+  unsigned long long flips;          // diagnostics
+  unsigned long long flips_unflagged;
+  unsigned long long flagged;
+  unsigned int max_dp_bits;          // float bits of max |p32 - p64|
+  unsigned int pad1;
+};
+
+struct Chunks {
+  const int32_t* rep;    // [n]
+  const int32_t* begin;  // [n]
+  int32_t n;
+};
+
+struct StepArgs {
+  RepDev* reps;          // [n_rep] device
+  int32_t n_rep;
+  Ctl* ctl;              // device
+  int32_t* n_slots;      // [n_rep] slots in use (agents, alive or not yet compacted)
+  int32_t* exited;       // [n_rep] agents that left through an exit, total
+  uint32_t* queue;       // [q_cap] FP64 re-check queue (rep << 24 | slot)
+  uint32_t q_cap;
+  uint32_t* act[3];      // movement work lists (rep << 24 | slot)
+  uint32_t act_cap;
+  unsigned long long* dig_cell;  // [dig_cap * n_rep] per-step digests (optional)
+  unsigned long long* dig_des;
+  int32_t dig_cap;
+  // Morton re-sort scratch: [n_buckets + 1] offsets, then 2 words per replicate
+  uint32_t* bucket_count;
+  int32_t n_buckets;
+  // diagnostics
+  float* diag_p32;         // [total slots * kMaxK] FP32 cumulative probabilities
+  int32_t* diag_choice32;  // [total slots]
+  uint8_t* diag_flag;      // [total slots]
+  int64_t* diag_base;      // [n_rep] offset of each replicate's slots in the diag arrays
+};
+
+// ---- launch wrappers (defined in the .cu files) ---------------------------
+int plan_groups_launch(const StepArgs& a, int v, int reach, int lanes, int precision,
+                       const Chunks& ch, int grid, cudaStream_t s, bool diag);
+int plan_recheck_launch(const StepArgs& a, int grid, cudaStream_t s);
+int plan_diag_compare_launch(const StepArgs& a, int v, int reach, const Chunks& ch, int grid,
+                             cudaStream_t s);
+int move_prep_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s);
+int move_rounds_launch(const StepArgs& a, int grid, int block, cudaStream_t s);
+int move_rounds_max_grid(int block, int* grid_out);
+int step_end_launch(const StepArgs& a, cudaStream_t s);
+int step_begin_launch(const StepArgs& a, cudaStream_t s);
+int digest_des_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s);
+int digest_cell_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s);
+int resort_launch(const StepArgs& a, const Chunks& ch, int grid, bool force, cudaStream_t s);
+int masks_launch(const RepDev& host_rep, RepDev* dev_rep, int64_t cells, cudaStream_t s);
+int clear_occ_launch(RepDev* dev_rep, const int32_t* n_slots_dev, int rep, int cap,
+                     cudaStream_t s);
+int place_launch(RepDev* dev_rep, const int32_t* cells, const int32_t* ids, int n,
+                 cudaStream_t s);
+int gather_by_id_launch(const RepDev* dev_rep, const int32_t* n_slots_dev, int rep, int cap,
+                        int32_t* out_cell, int32_t* out_desired, int32_t bound,
+                        cudaStream_t s);
+int union_count_launch(const RepDev* dev_rep, const int32_t* n_slots_dev, int rep, int cap,
+                       int v, int reach, int W, int H, uint32_t* bitmap,
+                       unsigned long long* out, cudaStream_t s);
+int test_exp64_launch(const double* x, double* y, int64_t n, cudaStream_t s);
+int test_philox_launch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
+                       cudaStream_t s);
+int test_ex2_launch(float lo, float hi, unsigned long long* out_max_rel_bits, cudaStream_t s);
+int test_barrier_timeout_launch(Ctl* ctl, int grid, cudaStream_t s);
+
+}  // namespace fastgb

@@ -1,0 +1,390 @@
+// plan_kernels.cuh -- planning phase of the F.A.S.T. step: every agent draws its desired
+// cell from the static floor field and the occupancy at the start of the step
+// (Kretz, Sec. 1: the planning phase only reads data common to all agents;
+// Sec. 2: k_S = 1.2, k_other = 0).
+//
+//   k_plan_fp32<V,REACH,G>  G lanes per agent; FP32 weights exp(-k_S dS) on
+//                           the SFU, shuffle prefix sums over the G lanes,
+//                           Philox draw, margin test; draws that fall within
+//                           the margin of a cumulative boundary go to a queue
+//   k_recheck               one warp per queued agent, FP64 weights and the
+//                           sequential canonical-order sums of the FP64 rule
+//   k_plan_fp64<V,REACH>    one thread per agent, the FP64 rule for everyone
+//   k_diag_compare<V,REACH> FP64 rule vs the FP32 kernel's recorded choice,
+//                           flags and cumulative probabilities (diagnostics)
+#pragma once
+#include "fast_device.cuh"
+
+namespace fastgb {
+
+template <int V, int REACH>
+__host__ __device__ constexpr int reach_center() {
+  int k = 0;
+  for (int y = -V; y <= V; ++y)
+    for (int x = -V; x <= V; ++x) {
+      if (x == 0 && y == 0) return k;
+      k += reach_in(x, y, V, REACH) ? 1 : 0;
+    }
+  return -1;
+}
+
+// Canonical offsets of one reach set, as cell-index deltas for row length W.
+__device__ __forceinline__ void fill_offsets(int* s_off, int v, int reach, int W) {
+  if (threadIdx.x == 0) {
+    int k = 0;
+    for (int y = -v; y <= v; ++y)
+      for (int x = -v; x <= v; ++x)
+        if (reach_in(x, y, v, reach)) s_off[k++] = y * W + x;
+  }
+}
+
+// k-th canonical offset of a reach set (runtime v), as (dx, dy).
+__device__ __forceinline__ void kth_offset(int v, int reach, int k, int* dx, int* dy) {
+  for (int y = -v; y <= v; ++y) {
+    int row = 0;
+    for (int x = -v; x <= v; ++x) row += reach_in(x, y, v, reach) ? 1 : 0;
+    if (k < row) {
+      for (int x = -v; x <= v; ++x)
+        if (reach_in(x, y, v, reach)) {
+          if (k == 0) {
+            *dx = x;
+            *dy = y;
+            return;
+          }
+          --k;
+        }
+    }
+    k -= row;
+  }
+  *dx = 0;
+  *dy = 0;
+}
+
+__device__ __forceinline__ bool mask_bit(unsigned long long m0, unsigned long long m1, int k) {
+  return k < 64 ? ((m0 >> k) & 1ull) : ((m1 >> (k - 64)) & 1ull);
+}
+
+__device__ __forceinline__ void set_static(uint32_t* rec, int cell, uint32_t rec0, bool stays) {
+  rec[cell] = stays ? (rec0 | REC_STA) : (rec0 & ~REC_STA);
+}
+
+// ---------------------------------------------------------------------------
+// FP32 planning, G lanes per agent.  Lane `sub` of a group owns the
+// candidates [sub*Q, sub*Q + Q) of the canonical order.  Every cumulative
+// value the decision uses is a sum of at most K positive FP32 weights, so its
+// relative error is bounded by gamma = (1+delta)(1+2^-24)^K - 1 (delta: one
+// weight's error); the host folds this into the margin M.  A draw r = u*W
+// is accepted only if C_prev + M*W < r < C_k - M*W; otherwise the agent is
+// re-evaluated with the FP64 rule.
+template <int V, int REACH, int G, bool DIAG>
+__global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int norecheck) {
+  constexpr int K = reach_count(V, REACH);
+  constexpr int Q = (K + G - 1) / G;
+  constexpr int CENTER = reach_center<V, REACH>();
+  constexpr int PER_PASS = 256 / G;
+  __shared__ int s_off[K];
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int sub = lane & (G - 1);
+  const int grp = tid / G;
+  const unsigned gmask =
+      (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  const int t = a.ctl->t;
+  int cur_rep = -1;
+
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const int begin = ch.begin[c];
+    if (rep != cur_rep) {
+      __syncthreads();
+      fill_offsets(s_off, V, REACH, a.reps[rep].W);
+      __syncthreads();
+      cur_rep = rep;
+    }
+    const RepDev& R = a.reps[rep];
+    uint32_t* rec = R.rec;
+    const int end = min(begin + kChunk, a.n_slots[rep]);
+    const float c32 = R.c32;
+    for (int pass = 0; pass < G; ++pass) {
+      const int slot = begin + pass * PER_PASS + grp;
+      if (slot >= end) continue;
+      const int cell = R.cell[slot];
+      if (cell < 0) continue;
+      const uint32_t rec0 = rec[cell];
+      const int a0 = rec_a(rec0), b0 = rec_b(rec0);
+      const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
+      const unsigned long long m1 = (K > 64) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
+
+      float w[Q];
+      float lsum = 0.f;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        const int k = sub * Q + j;
+        float wk = 0.f;
+        if (k < K && mask_bit(m0, m1, k)) {
+          if (k == CENTER) {
+            wk = 1.0f;
+          } else {
+            const uint32_t r = rec[cell + s_off[k]];
+            if (!(r & REC_OCC)) wk = ex2_approx(ds32(rec_a(r) - a0, rec_b(r) - b0) * c32);
+          }
+        }
+        w[j] = wk;
+        lsum += wk;
+      }
+      // inclusive / exclusive scan of the lane sums inside the group
+      float incl = lsum;
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) {
+        const float tv = __shfl_up_sync(gmask, incl, o, G);
+        if (sub >= o) incl += tv;
+      }
+      float excl = __shfl_up_sync(gmask, incl, 1, G);
+      if (sub == 0) excl = 0.f;
+      const float Wt = __shfl_sync(gmask, incl, G - 1, G);
+      const int id = R.id[slot];
+      float uf = 0.f;
+      if (sub == 0) uf = (float)plan_uniform((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
+      uf = __shfl_sync(gmask, uf, 0, G);
+      const float r = __fmul_rn(uf, Wt);
+
+      // walk the lane's candidates: first k with r < C_k
+      float cacc = excl, cprev = 0.f, ck = 0.f, clast_prev = excl;
+      int found = -1, lastnz = -1;
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        if (w[j] > 0.f) {
+          const float cn = cacc + w[j];
+          if (found < 0 && r < cn) {
+            found = sub * Q + j;
+            cprev = cacc;
+            ck = cn;
+          }
+          clast_prev = cacc;
+          lastnz = sub * Q + j;
+          cacc = cn;
+        }
+      }
+      if (DIAG) {
+        float* dp = a.diag_p32 + (a.diag_base[rep] + slot) * (int64_t)kMaxK;
+        float cc = excl;
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+          const int k = sub * Q + j;
+          cc = (w[j] > 0.f) ? cc + w[j] : cc;
+          if (k < K) dp[k] = cc / Wt;
+        }
+      }
+      const unsigned fb = __ballot_sync(gmask, found >= 0) & gmask;
+      int owner;
+      bool any = fb != 0u;
+      if (any) {
+        owner = __ffs(fb) - 1;
+      } else {
+        const unsigned nb = __ballot_sync(gmask, lastnz >= 0) & gmask;
+        owner = 31 - __clz(nb);
+      }
+      if (lane == owner) {
+        int kk;
+        bool ok;
+        if (any) {
+          kk = found;
+          const float mw = R.margin * Wt;
+          ok = (r > cprev + mw) && (r < ck - mw);
+        } else {
+          kk = lastnz;
+          ok = false;
+          (void)clast_prev;
+        }
+        const int target = cell + s_off[kk];
+        if (DIAG) {
+          const int64_t di = a.diag_base[rep] + slot;
+          a.diag_choice32[di] = target;
+          a.diag_flag[di] = ok ? 0 : 1;
+        }
+        if (ok || norecheck) {
+          R.desired[slot] = target;
+          set_static(rec, cell, rec0, target == cell);
+        } else {
+          const uint32_t qi = atomicAdd(&a.ctl->q_count, 1u);
+          if (qi < a.q_cap) a.queue[qi] = ((uint32_t)rep << 24) | (uint32_t)slot;
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 rule for one agent (thread-serial): weights in canonical order,
+// W and C_k summed sequentially, smallest k with fl(u*W) < C_k.
+template <int V, int REACH>
+__device__ __forceinline__ int plan_fp64_one(const RepDev& R, const int* s_off, int cell, int id,
+                                             int t, double* cum_out) {
+  constexpr int K = reach_count(V, REACH);
+  constexpr int CENTER = reach_center<V, REACH>();
+  const uint32_t* rec = R.rec;
+  const uint32_t rec0 = rec[cell];
+  const double S0 = s64_of(rec0);
+  const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
+  const unsigned long long m1 = (K > 64) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
+  const double nks = -R.kS;
+  double wk[K];
+  double W = 0.0;
+#pragma unroll 4
+  for (int k = 0; k < K; ++k) {
+    double w = 0.0;
+    if (mask_bit(m0, m1, k)) {
+      const uint32_t r = (k == CENTER) ? rec0 : rec[cell + s_off[k]];
+      if (k == CENTER || !(r & REC_OCC)) {
+        const double d = __dsub_rn(s64_of(r), S0);
+        w = exp64(__dmul_rn(nks, d));
+        W = __dadd_rn(W, w);
+      }
+    }
+    wk[k] = w;
+  }
+  const double u = plan_uniform((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
+  const double r = __dmul_rn(u, W);
+  double c = 0.0;
+  int chosen = -1, last = -1;
+  for (int k = 0; k < K; ++k) {
+    if (wk[k] > 0.0) {
+      c = __dadd_rn(c, wk[k]);
+      if (chosen < 0 && r < c) chosen = k;
+      last = k;
+    }
+    if (cum_out) cum_out[k] = c / W;
+  }
+  if (chosen < 0) chosen = last;
+  return cell + s_off[chosen];
+}
+
+template <int V, int REACH>
+__global__ void __launch_bounds__(128) k_plan_fp64(StepArgs a, Chunks ch) {
+  constexpr int K = reach_count(V, REACH);
+  __shared__ int s_off[K];
+  const int t = a.ctl->t;
+  int cur_rep = -1;
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const int begin = ch.begin[c];
+    if (rep != cur_rep) {
+      __syncthreads();
+      fill_offsets(s_off, V, REACH, a.reps[rep].W);
+      __syncthreads();
+      cur_rep = rep;
+    }
+    const RepDev& R = a.reps[rep];
+    const int end = min(begin + kChunk, a.n_slots[rep]);
+    for (int slot = begin + threadIdx.x; slot < end; slot += blockDim.x) {
+      const int cell = R.cell[slot];
+      if (cell < 0) continue;
+      const uint32_t rec0 = R.rec[cell];
+      const int target = plan_fp64_one<V, REACH>(R, s_off, cell, R.id[slot], t, nullptr);
+      R.desired[slot] = target;
+      set_static(R.rec, cell, rec0, target == cell);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: FP64 rule for every agent against the FP32 kernel's recorded
+// choice (no re-check), flag and cumulative probabilities.
+template <int V, int REACH>
+__global__ void __launch_bounds__(128) k_diag_compare(StepArgs a, Chunks ch) {
+  constexpr int K = reach_count(V, REACH);
+  __shared__ int s_off[K];
+  const int t = a.ctl->t;
+  int cur_rep = -1;
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const int begin = ch.begin[c];
+    if (rep != cur_rep) {
+      __syncthreads();
+      fill_offsets(s_off, V, REACH, a.reps[rep].W);
+      __syncthreads();
+      cur_rep = rep;
+    }
+    const RepDev& R = a.reps[rep];
+    const int end = min(begin + kChunk, a.n_slots[rep]);
+    for (int slot = begin + threadIdx.x; slot < end; slot += blockDim.x) {
+      const int cell = R.cell[slot];
+      if (cell < 0) continue;
+      double cum[K];
+      const int target = plan_fp64_one<V, REACH>(R, s_off, cell, R.id[slot], t, cum);
+      const int64_t di = a.diag_base[rep] + slot;
+      const int t32 = a.diag_choice32[di];
+      const bool flagged = a.diag_flag[di] != 0;
+      if (flagged) atomicAdd(&a.ctl->flagged, 1ull);
+      if (t32 != target) {
+        atomicAdd(&a.ctl->flips, 1ull);
+        if (!flagged) atomicAdd(&a.ctl->flips_unflagged, 1ull);
+      }
+      const float* dp = a.diag_p32 + di * (int64_t)kMaxK;
+      float mx = 0.f;
+      for (int k = 0; k < K; ++k) mx = fmaxf(mx, (float)fabs((double)dp[k] - cum[k]));
+      atomicMax(&a.ctl->max_dp_bits, __float_as_uint(mx));
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int V, int REACH>
+static int launch_fp32(const StepArgs& a, int lanes, const Chunks& ch, int grid, cudaStream_t s,
+                       bool diag, int norecheck) {
+#define FAST_L(G)                                                                  \
+  if (lanes == G) {                                                                \
+    if (diag)                                                                      \
+      k_plan_fp32<V, REACH, G, true><<<grid, 256, 0, s>>>(a, ch, norecheck);       \
+    else                                                                           \
+      k_plan_fp32<V, REACH, G, false><<<grid, 256, 0, s>>>(a, ch, norecheck);      \
+    return 0;                                                                      \
+  }
+  FAST_L(1)
+  FAST_L(2)
+  FAST_L(4)
+  FAST_L(8)
+#undef FAST_L
+  return -1;
+}
+
+template <int V, int REACH>
+static int launch_v(const StepArgs& a, int lanes, int precision, const Chunks& ch, int grid,
+                    cudaStream_t s, bool diag) {
+  if (precision == PREC_FP64) {
+    k_plan_fp64<V, REACH><<<grid, 128, 0, s>>>(a, ch);
+    return 0;
+  }
+  return launch_fp32<V, REACH>(a, lanes, ch, grid, s, diag,
+                               (precision == PREC_FP32_NORECHECK || diag) ? 1 : 0);
+}
+
+// All reach variants of one v_m (one translation unit per v_m).
+template <int V>
+static int launch_one_v(const StepArgs& a, int reach, int lanes, int precision, const Chunks& ch,
+                        int grid, cudaStream_t s, bool diag) {
+  if (reach == REACH_L2) return launch_v<V, REACH_L2>(a, lanes, precision, ch, grid, s, diag);
+  if (reach == REACH_L2P) return launch_v<V, REACH_L2P>(a, lanes, precision, ch, grid, s, diag);
+  if (reach == REACH_LINF) return launch_v<V, REACH_LINF>(a, lanes, precision, ch, grid, s, diag);
+  return -1;
+}
+
+template <int V>
+static int diag_one_v(const StepArgs& a, int reach, const Chunks& ch, int grid, cudaStream_t s) {
+  if (reach == REACH_L2) {
+    k_diag_compare<V, REACH_L2><<<grid, 128, 0, s>>>(a, ch);
+    return 0;
+  }
+  if (reach == REACH_L2P) {
+    k_diag_compare<V, REACH_L2P><<<grid, 128, 0, s>>>(a, ch);
+    return 0;
+  }
+  if (reach == REACH_LINF) {
+    k_diag_compare<V, REACH_LINF><<<grid, 128, 0, s>>>(a, ch);
+    return 0;
+  }
+  return -1;
+}
+
+}  // namespace fastgb

@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Desired cells and trajectories must be identical (bit-exact integers) for
+every agent and step: the FP64 planning path replays the oracle's FP64
+sequence, and the FP32 path re-evaluates in FP64 every draw that falls within
+its error margin of a cumulative boundary.  Whole arrays are compared on
+small grids; per-step digests (splitmix64 sums over (id, cell) and
+(id, desired)) plus final arrays on the larger ones.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_0911_2900_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+REACH_ORC = {"l2": 0, "l2p": 1, "linf": 2}
+
+
+@pytest.fixture(scope="module")
+def fg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    import paper_0911_2900_gb300 as fg
+
+    fg.load()
+    return fg
+
+
+def run_gpu(fg, works, steps, precision="fp32_recheck", reach="l2", digests=True, resort=8,
+            graph=True, id_perm=None, start_step=0, lanes=None, tile_shift=None):
+    ctx = fg.Context(len(works), precision, reach)
+    ctx.set_option("digests", 1 if digests else 0)
+    ctx.set_option("resort_period", resort)
+    ctx.set_option("use_graph", 1 if graph else 0)
+    if tile_shift is not None:
+        ctx.set_option("tile_shift", tile_shift)
+    if lanes is not None:
+        for v, g in lanes.items():
+            ctx.set_option(f"lanes_v{v}", g)
+    for r, w in enumerate(works):
+        ctx.init_grid(r, w.cell_type, w.k_S, w.v_m, w.seed)
+        if id_perm is None:
+            ctx.place(r, w.cells, start_step=start_step)
+        else:
+            ctx.place(r, w.cells[id_perm], ids=id_perm.astype(np.int32), start_step=start_step)
+    ctx.step(steps)
+    out = []
+    for r, w in enumerate(works):
+        cells, des, st = ctx.readback(r, len(w.cells))
+        dc, dd = ctx.digests(r, steps) if digests else (None, None)
+        out.append(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd))
+    return ctx, out
+
+
+def run_oracle(orc, w, steps, reach="l2", t0=0, threads=None):
+    sim = orc.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed, reach=REACH_ORC[reach])
+    sim.place(w.cells)
+    r = sim.run(t0, steps, threads=threads or min(8, os.cpu_count() or 1))
+    cells = sim.cells_by_id()
+    return dict(cells=cells, desired=r["desired"], dig_cell=r["dig_cell"],
+                dig_des=r["dig_des"], alive=r["alive"], sim=sim)
+
+
+def assert_same(g, o, steps):
+    assert len(g["dig_cell"]) == steps
+    bad = np.flatnonzero(g["dig_des"] != o["dig_des"])
+    assert len(bad) == 0, f"desired digests differ first at step {bad[0]}"
+    bad = np.flatnonzero(g["dig_cell"] != o["dig_cell"])
+    assert len(bad) == 0, f"cell digests differ first at step {bad[0]}"
+    assert np.array_equal(g["cells"], o["cells"])
+    alive = o["cells"] >= 0
+    assert np.array_equal(g["desired"][alive], o["desired"][alive])
+    assert g["stats"]["alive"] == int(alive.sum())
+
+
+# --------------------------------------------------------------------------- self tests
+def test_exp64_bitwise_equal_to_oracle(fg, orc):
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-13, 13, 200_000), rng.uniform(-700, 700, 20_000),
+                        np.array([0.0, -0.0, 1.0, -1.0, 0.5, -0.5])])
+    y = fg.selftest_exp64(x)
+    want = np.array([orc.exp64(float(v)) for v in x])
+    assert np.array_equal(y.view(np.uint64), want.view(np.uint64))
+
+
+def test_philox_bitwise_equal_to_oracle(fg, orc):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, (5000, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (5000, 2), dtype=np.uint64).astype(np.uint32)
+    out = fg.selftest_philox(ctr, key)
+    for i in range(0, 5000, 7):
+        assert out[i].tolist() == orc.philox(ctr[i], key[i]).tolist()
+
+
+def test_ex2_error_within_margin_budget(fg):
+    """The margin assumes the SFU 2^y has relative error <= 2^-21 on the
+    weights' argument range; measure it exhaustively and demand a factor 2."""
+    err = fg.selftest_ex2(-16.0, 16.0)
+    assert err <= 2.0 ** -22, err
+
+
+def test_bounded_barrier_reports_timeout(fg):
+    assert fg.selftest_barrier_timeout(2_000_000) == -5
+
+
+# --------------------------------------------------------------------------- parity
+@pytest.mark.parametrize("precision", ["fp64", "fp32_recheck"])
+def test_room200_2k_v4(fg, orc, precision):
+    w = wl.config_small_room()
+    steps = 396 if precision == "fp64" else 120
+    _, (g,) = run_gpu(fg, [w], steps, precision)
+    o = run_oracle(orc, w, steps)
+    assert_same(g, o, steps)
+
+
+@pytest.mark.parametrize("v", [1, 2, 3, 4, 5])
+def test_corridors_40k_vsweep_fp64(fg, orc, v):
+    w = wl.config_corridors(v_m=v)
+    steps = 12
+    _, (g,) = run_gpu(fg, [w], steps, "fp64")
+    o = run_oracle(orc, w, steps)
+    assert_same(g, o, steps)
+
+
+@pytest.mark.parametrize("v", [1, 3, 5])
+def test_corridors_40k_fp32_recheck(fg, orc, v):
+    w = wl.config_corridors(v_m=v)
+    steps = 12
+    _, (g,) = run_gpu(fg, [w], steps, "fp32_recheck")
+    o = run_oracle(orc, w, steps)
+    assert_same(g, o, steps)
+
+
+@pytest.mark.parametrize("reach", ["l2p", "linf"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_recheck"])
+def test_reach_variants(fg, orc, reach, precision):
+    w = wl.config_small_room(W=90, H=70, n=1500, seed=4, v_m=5 if reach == "linf" else 3)
+    steps = 40
+    _, (g,) = run_gpu(fg, [w], steps, precision, reach=reach)
+    o = run_oracle(orc, w, steps, reach=reach)
+    assert_same(g, o, steps)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+def test_lanes_per_agent_variants(fg, orc, lanes):
+    w = wl.config_small_room(W=120, H=90, n=3001, seed=5, v_m=4)
+    steps = 25
+    _, (g,) = run_gpu(fg, [w], steps, "fp32_recheck", lanes={4: lanes})
+    o = run_oracle(orc, w, steps)
+    assert_same(g, o, steps)
+
+
+def test_storage_order_graph_and_resort_do_not_matter(fg, orc):
+    w = wl.config_small_room(W=100, H=100, n=2500, seed=6, v_m=4)
+    steps = 30
+    o = run_oracle(orc, w, steps)
+    perm = np.random.default_rng(3).permutation(len(w.cells))
+    for kw in (dict(), dict(id_perm=perm), dict(graph=False), dict(resort=0), dict(resort=1),
+               dict(tile_shift=2)):
+        _, (g,) = run_gpu(fg, [w], steps, "fp32_recheck", **kw)
+        assert_same(g, o, steps)
+
+
+def test_batched_replicates(fg, orc):
+    works = wl.config_batch(n_rep=6, seed=3, cells_hi=300 ** 2, agents_hi=6000)
+    steps = 30
+    _, gs = run_gpu(fg, works, steps, "fp32_recheck")
+    for w, g in zip(works, gs):
+        assert_same(g, run_oracle(orc, w, steps), steps)
+
+
+def test_resume_is_bit_exact(fg, orc):
+    w = wl.config_small_room(W=80, H=80, n=1200, seed=8, v_m=4)
+    ctx, (g20,) = run_gpu(fg, [w], 20, "fp32_recheck", digests=False)
+    ctx1, (g10,) = run_gpu(fg, [w], 10, "fp32_recheck", digests=False)
+    alive = np.flatnonzero(g10["cells"] >= 0).astype(np.int32)
+    ctx2 = fg.Context(1, "fp32_recheck")
+    ctx2.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx2.place(0, g10["cells"][alive], ids=alive, start_step=10)
+    ctx2.step(10)
+    cells, _, st = ctx2.readback(0, len(w.cells))
+    assert np.array_equal(cells, g20["cells"])
+
+
+def test_edge_cases(fg, orc):
+    # no agents at all
+    t = wl.room(30, 20)
+    wl.add_exit(t, "bottom", 10, 4)
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.init_grid(0, t, 1.2, 4, 0)
+    ctx.place(0, np.zeros(0, np.int32))
+    ctx.step(3)
+    cells, des, st = ctx.readback(0, 0)
+    assert st["alive"] == 0
+    # one agent next to the exit leaves
+    w = wl.Workload("one", t, np.array([18 * 30 + 11], np.int32), 4, seed=2)
+    _, (g,) = run_gpu(fg, [w], 5, "fp32_recheck")
+    o = run_oracle(orc, w, 5)
+    assert_same(g, o, 5)
+    # a packed room (every free cell taken but a few): rounds with long chains
+    t2 = wl.room(24, 24)
+    wl.add_exit(t2, "left", 10, 3)
+    free = np.flatnonzero(t2.ravel() == wl.FREE)
+    cells = np.sort(np.random.default_rng(0).choice(free, len(free) - 9, replace=False))
+    w2 = wl.Workload("packed", t2, cells.astype(np.int32), 5, seed=4)
+    _, (g2,) = run_gpu(fg, [w2], 60, "fp32_recheck")
+    assert_same(g2, run_oracle(orc, w2, 60), 60)
+    # k_S = 0 (uniform choice)
+    w3 = wl.config_small_room(W=50, H=40, n=300, seed=2, v_m=3)
+    w3.k_S = 0.0
+    _, (g3,) = run_gpu(fg, [w3], 20, "fp32_recheck")
+    assert_same(g3, run_oracle(orc, w3, 20), 20)
+
+
+def test_invalid_inputs_are_rejected(fg):
+    t = wl.room(20, 20)
+    wl.add_exit(t, "top", 5, 2)
+    ctx = fg.Context(1, "fp32_recheck")
+    with pytest.raises(fg.FastError):
+        ctx.place(0, [25])                      # grid not set
+    with pytest.raises(fg.FastError):
+        ctx.init_grid(0, t, 1.2, 6, 0)          # v_m out of range
+    with pytest.raises(fg.FastError):
+        ctx.init_grid(0, wl.room(20, 20), 1.2, 4, 0)   # no exit
+    ctx.init_grid(0, t, 1.2, 4, 0)
+    for bad in ([0], [5], [25, 25], [20 * 20]):  # wall, exit, duplicate, outside
+        with pytest.raises(fg.FastError):
+            ctx.place(0, bad)
+    with pytest.raises(fg.FastError):
+        ctx.place(0, [25, 26], ids=[3, 3])     # duplicate ids
+    with pytest.raises(fg.FastError):
+        ctx.place(0, [25], ids=[1 << 24])      # id too large
+    ctx.place(0, [25, 47])
+    ctx.step(2)
+    ctx.readback(0)
+
+
+# --------------------------------------------------------------------------- full size
+def test_precision_form_full_size_one_step(fg, orc):
+    """4000x4000, 1M clustered agents, v_m=4, FP32 + FP64 re-check, in the
+    launch configuration the benchmark times: after 3 steps, the next step's
+    desired cells and positions equal the oracle's for every agent; the
+    FP32-only draw flips only inside the margin."""
+    w = wl.config_precision()
+    ctx, (g3,) = run_gpu(fg, [w], 3, "fp32_recheck", digests=False)
+    rep = ctx.precision_report()
+    assert rep["flips_unflagged"] == 0
+    assert rep["flagged"] < 0.01 * rep["agents"]
+    alive = np.flatnonzero(g3["cells"] >= 0).astype(np.int32)
+    sim = orc.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed)
+    sim.place(g3["cells"][alive], ids=alive)
+    ctx.step(1)
+    cells, des, _ = ctx.readback(0, len(w.cells))
+    r = sim.run(3, 1, threads=os.cpu_count() or 1, digests=False)
+    want_des = np.full(len(w.cells), -1, np.int32)
+    want_des[alive] = r["desired"]
+    assert np.array_equal(des[cells >= 0], want_des[cells >= 0])
+    assert np.array_equal(cells, sim.cells_by_id())
