@@ -274,6 +274,7 @@ def bench_ours(args):
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     _, _, st1 = ctx.readback(0, 0)
+    mv_wait, mv_us = ctx.move_profile()
     u1 = ctx.reach_union(0)
     agent_steps = st1["agent_steps"] - st0["agent_steps"]
     launches = st1["kernel_launches"] - st0["kernel_launches"]
@@ -372,6 +373,9 @@ def bench_ours(args):
                          "move": statistics.mean(move_ms), "other": statistics.mean(other_ms)},
             "rechecked_per_step": (st1["rechecked"] - st0["rechecked"]) / args.steps,
             "move_rounds_per_step": (st1["move_rounds"] - st0["move_rounds"]) / args.steps,
+            "move_last_step": {"waiting_after_round": [int(x) for x in mv_wait[:12]],
+                               "round_us": [round(float(x), 2) for x in mv_us[:12]],
+                               "rounds": int(len(mv_wait))},
             "roofline": {"bound": "hbm", "kernel": "k_plan_fp32", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_kind": peak_kind,

@@ -168,6 +168,12 @@ int fast_get_digests(fast_ctx* ctx, int32_t replicate, int32_t max_steps, uint64
  * Errors: FAST_ESTATE if no step has run. */
 int fast_phase_times(fast_ctx* ctx, float* ms4);
 
+/* Movement rounds of the last step (waits for the stream): n_wait[r] = agents
+ * still waiting after round r's claims, t_ns[r] = device global timer at the
+ * start of round r (t_ns has one entry more).  Writes min(max_rounds, 64)
+ * rounds; returns the number of rounds of the step or a negative error. */
+int fast_move_profile(fast_ctx* ctx, int32_t max_rounds, uint32_t* n_wait, uint64_t* t_ns);
+
 /* Runs the FP32 planning of the current state without re-check next to the
  * FP64 rule and compares them (does not change the state).  Errors:
  * FAST_ESTATE (precision is FAST_FP64 or no agents), FAST_ENOMEM, FAST_ECUDA. */
@@ -188,6 +194,11 @@ int fast_selftest_exp64(const double* x, double* y, int64_t n);
 int fast_selftest_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n);
 /* Largest relative error of the SFU 2^y over every float y in [lo, hi]. */
 int fast_selftest_ex2(float lo, float hi, double* max_rel_err);
+/* Average time of the library's grid barrier: a cooperative kernel of
+ * `blocks` x `threads` (all resident) runs `iters` barriers in a row.
+ * Returns FAST_EINVAL if the grid cannot be co-resident. */
+int fast_selftest_barrier_cost(int32_t blocks, int32_t threads, int32_t iters,
+                               double* ns_per_barrier);
 /* Runs a cooperative kernel whose grid barrier can never complete, with a
  * wait limit of limit_ns; returns FAST_ETIMEOUT when the wait gave up (the
  * expected outcome) and leaves the CUDA context usable. */

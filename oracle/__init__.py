@@ -71,7 +71,7 @@ def lib():
                 "orc_build_occ": (i32, [vp, i32, vp, vp]),
                 "orc_plan_agent": (i32, [vp, vp, i32, i32, i32, vp, vp]),
                 "orc_plan_all": (None, [vp, vp, i32, vp, vp, i32, vp, i32]),
-                "orc_move_priority": (u64, [u64, i32, i32]),
+                "orc_move_priority": (C.c_uint32, [u64, i32, i32]),
                 "orc_move": (i32, [vp, vp, i32, vp, vp, vp, i32]),
                 "orc_digest": (u64, [i32, vp, vp]),
                 "orc_run": (i32, [vp, vp, i32, vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, vp]),

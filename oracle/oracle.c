@@ -356,25 +356,45 @@ void orc_plan_all(const orc_world* w, const int32_t* occ, int32_t n, const int32
 }
 
 /* ------------------------------------------------------------------------- */
-/* Movement order (reading R7): Philox(key = seed, ctr = (id, t, 1, 0)) gives
- * the 64-bit key (x0 << 32) | x1; agents move in ascending order of its top
- * 40 bits, ties broken by id: priority = (key >> 24) << 24 | id (id < 2^24). */
-uint64_t orc_move_priority(uint64_t seed, int32_t id, int32_t t) {
-  uint32_t ctr[4] = {(uint32_t)id, (uint32_t)t, 1u, 0u};
+/* Movement order (reading R7): a fresh pseudo-random permutation of the
+ * agents every step.  The step key (k0, k1) is the first two words of
+ * Philox(key = seed, ctr = (0, t, 2, 0)); agent id gets the priority
+ *   pi_t(id) = fmix32(fmix32(id ^ k0) ^ k1)
+ * with fmix32 the finalizer of MurmurHash3 (A. Appleby): xor-shifts and
+ * multiplications by odd constants, each a bijection of the 32-bit words, so
+ * pi_t is a bijection and no two agents share a priority.  Agents move in
+ * ascending priority. */
+static uint32_t orc_fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+static void orc_step_key(uint64_t seed, int32_t t, uint32_t* k0, uint32_t* k1) {
+  uint32_t ctr[4] = {0u, (uint32_t)t, 2u, 0u};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
   uint32_t rnd[4];
   orc_philox4x32_10(ctr, key, rnd);
-  uint64_t k64 = ((uint64_t)rnd[0] << 32) | rnd[1];
-  return ((k64 >> 24) << 24) | (uint64_t)(uint32_t)id;
+  *k0 = rnd[0];
+  *k1 = rnd[1];
+}
+
+uint32_t orc_move_priority(uint64_t seed, int32_t id, int32_t t) {
+  uint32_t k0, k1;
+  orc_step_key(seed, t, &k0, &k1);
+  return orc_fmix32(orc_fmix32((uint32_t)id ^ k0) ^ k1);
 }
 
 typedef struct {
-  uint64_t p;
+  uint32_t p;
   int32_t i;
 } orc_pi;
 
 static int cmp_pi(const void* x, const void* y) {
-  uint64_t a = ((const orc_pi*)x)->p, b = ((const orc_pi*)y)->p;
+  uint32_t a = ((const orc_pi*)x)->p, b = ((const orc_pi*)y)->p;
   return a < b ? -1 : (a > b ? 1 : 0);
 }
 
@@ -387,9 +407,11 @@ int32_t orc_move(const orc_world* w, int32_t* occ, int32_t n, const int32_t* id,
                  const int32_t* desired, int32_t t) {
   orc_pi* order = (orc_pi*)malloc((size_t)(n > 0 ? n : 1) * sizeof(orc_pi));
   int32_t m = 0;
+  uint32_t k0, k1;
+  orc_step_key(w->seed, t, &k0, &k1);
   for (int32_t i = 0; i < n; ++i)
     if (cell[i] >= 0) {
-      order[m].p = orc_move_priority(w->seed, id[i], t);
+      order[m].p = orc_fmix32(orc_fmix32((uint32_t)id[i] ^ k0) ^ k1);
       order[m].i = i;
       ++m;
     }

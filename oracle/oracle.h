@@ -75,8 +75,9 @@ void orc_plan_all(const orc_world* w, const int32_t* occ, int32_t n,
                   const int32_t* id, const int32_t* cell, int32_t t,
                   int32_t* desired, int32_t threads);
 
-/* Movement priority of agent id at step t (smaller moves earlier). */
-uint64_t orc_move_priority(uint64_t seed, int32_t id, int32_t t);
+/* Movement priority of agent id at step t (smaller moves earlier; a
+ * bijection of the id for each step). */
+uint32_t orc_move_priority(uint64_t seed, int32_t id, int32_t t);
 
 /* Sequential movement of all agents in priority order.  Updates cell (-1 when
  * an agent leaves through an exit) and occ.  Returns the number that left. */

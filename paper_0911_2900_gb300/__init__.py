@@ -76,6 +76,7 @@ EXPORTS = {
     "fast_get_digests": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p]),
     "fast_phase_times": (C.c_int, [C.c_void_p, C.c_void_p]),
     "fast_precision_report_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "fast_move_profile": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "fast_reach_union": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fast_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "fast_last_error": (C.c_char_p, [C.c_void_p]),
@@ -84,6 +85,7 @@ EXPORTS = {
     "fast_selftest_philox": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64]),
     "fast_selftest_ex2": (C.c_int, [C.c_float, C.c_float, C.c_void_p]),
     "fast_selftest_barrier_timeout": (C.c_int, [C.c_int64]),
+    "fast_selftest_barrier_cost": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
 }
 
 
@@ -234,6 +236,15 @@ class Context:
         self._check(self.lib.fast_phase_times(self.h, ms), "fast_phase_times")
         return tuple(ms)
 
+    def move_profile(self):
+        """(waiting agents after each round's claims, round durations in us) of the last step."""
+        n_wait = np.zeros(64, np.uint32)
+        t_ns = np.zeros(65, np.uint64)
+        r = self._check(self.lib.fast_move_profile(self.h, 64, _ptr(n_wait), _ptr(t_ns)),
+                        "fast_move_profile")
+        m = min(r, 64)
+        return n_wait[:m].copy(), np.diff(t_ns[:m + 1].astype(np.float64)) / 1e3
+
     def precision_report(self):
         r = PrecisionReport()
         self._check(self.lib.fast_precision_report_run(self.h, C.byref(r)),
@@ -277,6 +288,15 @@ def selftest_ex2(lo: float, hi: float) -> float:
     rc = lib.fast_selftest_ex2(C.c_float(lo), C.c_float(hi), C.byref(v))
     if rc:
         raise FastError(rc, "fast_selftest_ex2")
+    return v.value
+
+
+def selftest_barrier_cost(blocks: int, threads: int, iters: int = 1000) -> float:
+    """Average ns per grid barrier of the library's cooperative kernels."""
+    v = C.c_double()
+    rc = load().fast_selftest_barrier_cost(int(blocks), int(threads), int(iters), C.byref(v))
+    if rc:
+        raise FastError(rc, "fast_selftest_barrier_cost")
     return v.value
 
 

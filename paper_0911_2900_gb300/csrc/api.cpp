@@ -70,7 +70,11 @@ struct fast_ctx {
   int32_t* d_nslots = nullptr;
   int32_t* d_exited = nullptr;
   uint32_t* d_queue = nullptr;
-  uint32_t* d_act[3] = {nullptr, nullptr, nullptr};
+  MoveEntry* d_act[3] = {nullptr, nullptr, nullptr};
+  uint32_t* d_act_info[3] = {nullptr, nullptr, nullptr};
+  uint32_t* d_mv_prio = nullptr;
+  uint32_t* d_mv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+
   uint32_t list_cap = 0;
   uint32_t* d_bucket = nullptr;
   int32_t n_buckets = 0;
@@ -304,12 +308,16 @@ int rebuild_layout(fast_ctx* c) {
   }
   if (total_cap > c->list_cap) {
     dfree(c, c->d_queue);
-    for (auto& p : c->d_act) dfree(c, p);
-    c->d_queue = nullptr;
-    c->d_act[0] = c->d_act[1] = c->d_act[2] = nullptr;
+    dfree(c, c->d_act[2]);
+    dfree(c, c->d_act_info[2]);
+    dfree(c, c->d_mv_prio);
+    for (auto& p : c->d_mv) dfree(c, p);
     const size_t n = (size_t)total_cap;
     if (int e = alloc_into(c, &c->d_queue, n)) return e;
-    for (auto& p : c->d_act)
+    if (int e = alloc_into(c, &c->d_act[2], n)) return e;
+    if (int e = alloc_into(c, &c->d_act_info[2], n)) return e;
+    if (int e = alloc_into(c, &c->d_mv_prio, n)) return e;
+    for (auto& p : c->d_mv)
       if (int e = alloc_into(c, &p, n)) return e;
     c->list_cap = (uint32_t)total_cap;
   }
@@ -335,7 +343,15 @@ StepArgs args_of(fast_ctx* c) {
   a.exited = c->d_exited;
   a.queue = c->d_queue;
   a.q_cap = c->list_cap;
-  for (int i = 0; i < 3; ++i) a.act[i] = c->d_act[i];
+  for (int i = 0; i < 3; ++i) {
+    a.act[i] = c->d_act[i];
+    a.act_info[i] = c->d_act_info[i];
+    a.mv_list[i] = c->d_mv[3 + i];
+  }
+  a.mv_prio = c->d_mv_prio;
+  a.mv_c0 = c->d_mv[0];
+  a.mv_ref = c->d_mv[1];
+  a.mv_info = c->d_mv[2];
   a.act_cap = c->list_cap;
   a.dig_cell = c->d_dig_cell;
   a.dig_des = c->d_dig_des;
@@ -349,14 +365,17 @@ Chunks all_chunks(fast_ctx* c) { return Chunks{c->d_all_rep, c->d_all_begin, c->
 
 int plan_grid(fast_ctx* c, int n_chunks) { return std::max(1, std::min(n_chunks, c->sms * 8)); }
 
+// Cooperative grid of the movement rounds: every block that can be resident
+// (the rounds are latency-bound), capped by the work and by the option.
 int move_grid(fast_ctx* c) {
   int g = 0;
-  if (move_rounds_max_grid(256, &g) != 0 || g <= 0) g = c->sms;
+  if (move_rounds_max_grid(1024, &g) != 0 || g <= 0) g = c->sms;
   if (c->move_blocks > 0) g = std::min(g, c->move_blocks);
-  const int need = std::max(1, (int)((c->list_cap + 255) / 256));
-  g = std::min(g, std::max(need, 1));
-  g = std::min(g, c->sms * 2);
   return std::max(g, 1);
+}
+
+int link_grid(fast_ctx* c) {
+  return std::max(1, std::min((int)((c->list_cap + 255) / 256), c->sms * 8));
 }
 
 // Inside a capture the record must be an external event-record node, so that
@@ -374,7 +393,7 @@ int enqueue_plan(fast_ctx* c, const StepArgs& a, bool diag, bool events) {
   }
   if (events) CUDA_TRY(c, record_event(c, 1));
   if (c->precision == FAST_FP32_RECHECK && !diag)
-    LAUNCH_TRY(c, plan_recheck_launch(a, std::max(1, c->sms), c->cur));
+    LAUNCH_TRY(c, plan_recheck_launch(a, std::max(1, c->sms * 4), c->cur));
   return FAST_OK;
 }
 
@@ -388,7 +407,7 @@ int enqueue_step(fast_ctx* c, bool resort) {
   CUDA_TRY(c, record_event(c, 2));
   if (c->digests) LAUNCH_TRY(c, digest_des_launch(a, all, plan_grid(c, all.n), c->cur));
   LAUNCH_TRY(c, move_prep_launch(a, all, plan_grid(c, all.n), c->cur));
-  LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), 256, c->cur));
+  LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), 1024, c->cur));
   CUDA_TRY(c, record_event(c, 3));
   if (c->digests) {
     LAUNCH_TRY(c, digest_cell_launch(a, all, plan_grid(c, all.n), c->cur));
@@ -562,11 +581,10 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   // (re)allocate the per-cell arrays
   dfree(c, R.d.rec);
   dfree(c, R.d.mask);
-  dfree(c, R.d.claim[0]);
-  dfree(c, R.d.claim[1]);
+  for (auto& p : R.d.claim) dfree(c, p);
   R.d.rec = nullptr;
   R.d.mask = nullptr;
-  R.d.claim[0] = R.d.claim[1] = nullptr;
+  R.d.claim[0] = R.d.claim[1] = R.d.claim[2] = nullptr;
   R.W = g->width;
   R.H = g->height;
   R.v = g->v_m;
@@ -576,8 +594,8 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   R.mw = R.K > 64 ? 2 : 1;
   if (int e = alloc_into(c, &R.d.rec, C)) return e;
   if (int e = alloc_into(c, &R.d.mask, C * R.mw)) return e;
-  if (int e = alloc_into(c, &R.d.claim[0], C)) return e;
-  if (int e = alloc_into(c, &R.d.claim[1], C)) return e;
+  for (auto& p : R.d.claim)
+    if (int e = alloc_into(c, &p, C)) return e;
   RepDev& d = R.d;
   d.W = R.W;
   d.H = R.H;
@@ -591,8 +609,7 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   d.seed_lo = (uint32_t)R.seed;
   d.seed_hi = (uint32_t)(R.seed >> 32);
   CUDA_TRY(c, cudaMemcpyAsync(d.rec, rec.data(), C * 4, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(d.claim[0], 0xFF, C * 8, c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(d.claim[1], 0xFF, C * 8, c->stream));
+  for (auto p : d.claim) CUDA_TRY(c, cudaMemsetAsync(p, 0xFF, C * 4, c->stream));
   R.grid_set = true;
   R.placed = false;
   R.n = 0;
@@ -841,6 +858,21 @@ int fast_phase_times(fast_ctx* c, float* ms4) {
   return FAST_OK;
 }
 
+int fast_move_profile(fast_ctx* c, int32_t max_rounds, uint32_t* n_wait, uint64_t* t_ns) {
+  if (!c || max_rounds < 0) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (int e = check_device_error(c)) return e;
+  Ctl h{};
+  CUDA_TRY(c, cudaMemcpy(&h, c->d_ctl, sizeof h, cudaMemcpyDeviceToHost));
+  const int n = std::min(std::min(max_rounds, kRoundLog), h.rounds_last);
+  for (int i = 0; i < n; ++i) {
+    if (n_wait) n_wait[i] = h.round_n[i];
+    if (t_ns) t_ns[i] = h.round_ns[i];
+  }
+  if (t_ns && n > 0) t_ns[n] = h.round_ns[n];
+  return h.rounds_last;
+}
+
 int fast_precision_report_run(fast_ctx* c, fast_precision_report* out) {
   if (!c || !out) return FAST_EINVAL;
   if (c->poisoned) return FAST_ESTATE;
@@ -1060,6 +1092,26 @@ int fast_selftest_ex2(float lo, float hi, double* max_rel_err) {
   std::memcpy(&v, &h, 8);
   *max_rel_err = v;
   return rc;
+}
+
+int fast_selftest_barrier_cost(int32_t blocks, int32_t threads, int32_t iters, double* ns_per_barrier) {
+  if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !ns_per_barrier) return FAST_EINVAL;
+  Ctl* d = nullptr;
+  if (cudaMalloc(&d, sizeof(Ctl)) != cudaSuccess) return FAST_ENOMEM;
+  Ctl h{};
+  h.barrier_ns_limit = 2000000000ull;
+  int rc = FAST_OK;
+  if (cudaMemcpy(d, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess) rc = FAST_ECUDA;
+  if (rc == FAST_OK && test_barrier_cost_launch(d, blocks, threads, iters, 0) != 0) rc = FAST_EINVAL;
+  if (rc == FAST_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FAST_ECUDA;
+  if (rc == FAST_OK && cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = FAST_ECUDA;
+  cudaGetLastError();
+  cudaFree(d);
+  if (rc != FAST_OK) return rc;
+  if (h.err != 0) return FAST_ETIMEOUT;
+  *ns_per_barrier = (double)h.round_ns[0] / iters;
+  return FAST_OK;
 }
 
 int fast_selftest_barrier_timeout(int64_t limit_ns) {

@@ -9,6 +9,7 @@
 // a = b = 0x7FFF marks walls and cells no exit can be reached from.  Exit
 // cells are the only cells with a = b = 0 and are never occupied.
 #pragma once
+#include <cooperative_groups.h>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -101,13 +102,29 @@ __device__ __forceinline__ double plan_uniform(uint32_t id, uint32_t t, uint32_t
   return __dmul_rn(__dadd_rn(__dmul_rn(hi, 67108864.0), lo), 0x1p-53);
 }
 
-// Movement priority: top 40 bits of the 64-bit word of the movement stream
-// (counter (id, t, 1, 0)), then the id; smaller moves earlier.
-__device__ __forceinline__ uint64_t move_priority(uint32_t id, uint32_t t, uint32_t k0,
-                                                  uint32_t k1) {
-  const U4 r = philox10(id, t, 1u, 0u, k0, k1);
-  const uint64_t k64 = ((uint64_t)r.x << 32) | r.y;
-  return ((k64 >> 24) << 24) | (uint64_t)id;
+// Movement order of step t: a keyed bijection of the agent id.  The step
+// key is the first two words of Philox(seed; (0, t, 2, 0)); the priority is
+// fmix32(fmix32(id ^ k0) ^ k1), fmix32 being MurmurHash3's finalizer (xor
+// shifts and odd multiplications, each invertible), so no two agents of a
+// replicate share a priority.  Smaller priorities move earlier.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+__device__ __forceinline__ uint32_t move_priority(uint32_t id, uint32_t k0, uint32_t k1) {
+  return fmix32(fmix32(id ^ k0) ^ k1);
+}
+
+__device__ __forceinline__ void move_step_key(uint32_t t, uint32_t s0, uint32_t s1, uint32_t* k0,
+                                              uint32_t* k1) {
+  const U4 r = philox10(0u, t, 2u, 0u, s0, s1);
+  *k0 = r.x;
+  *k1 = r.y;
 }
 
 // --------------------------------------------------------------------------
@@ -171,6 +188,16 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p) { return __ldcg(p); }
 __device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
   return __ldcg(p);
+}
+
+// Appends to a global list with one atomic per group of converged lanes:
+// returns this lane's slot (called only by the lanes that append).
+__device__ __forceinline__ uint32_t append_slot(uint32_t* counter) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  uint32_t base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(counter, (uint32_t)g.size());
+  return g.shfl(base, 0) + (uint32_t)g.thread_rank();
 }
 
 }  // namespace fastgb

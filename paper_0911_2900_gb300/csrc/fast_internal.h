@@ -16,6 +16,18 @@ constexpr int kChunk = 256;         // agents per work chunk
 constexpr int kMaxK = 121;          // largest reach set (L-infinity, v_m = 5)
 constexpr int kDevErrTimeout = 5;   // device error: a bounded wait gave up
 constexpr int kDevErrRounds = 6;    // device error: movement rounds exceeded the bound
+constexpr int kRoundLog = 64;       // movement rounds recorded per step
+constexpr int kMoveThreads = 1024;  // threads per block of the movement rounds
+constexpr int kMoveSmemCap = 8000;  // movers per block kept in shared memory (28 B each)
+
+// One mover of the current step (16 bytes): start cell, (replicate << 24 |
+// slot), movement priority, footprint info.
+struct alignas(16) MoveEntry {
+  uint32_t c0;
+  uint32_t ref;
+  uint32_t prio;
+  uint32_t info;
+};
 
 // Per-replicate descriptor, resident in device memory.
 struct RepDev {
@@ -30,14 +42,14 @@ struct RepDev {
   uint32_t seed_lo, seed_hi;
   uint32_t* rec;                    // [W*H] cell records
   unsigned long long* mask;         // [W*H*mw] line-of-sight masks
-  unsigned long long* claim[2];     // [W*H] movement claims (ping-pong)
+  uint32_t* claim[3];               // [W*H] movement claims (three in rotation)
   int32_t* id;                      // [cap]
   int32_t* cell;                    // [cap]  -1: slot empty / agent left
   int32_t* desired;                 // [cap]
   int32_t* id2;                     // [cap]  re-sort buffers
   int32_t* cell2;                   // [cap]
   unsigned long long* prio;         // [cap]  movement priority this step
-  uint32_t* mvinfo;                 // [cap]  footprint length | flags
+  uint32_t* mvinfo;                 // [cap]  scratch of the re-sort (desired cells)
 };
 
 // Step-wide control block, resident in device memory.
@@ -45,7 +57,8 @@ struct Ctl {
   int32_t t;                  // step index of the next step
   int32_t err;                // first device error (0 = none)
   uint32_t q_count;           // FP64 re-check queue length, this step
-  uint32_t act_count[3];      // movement list lengths (ping-pong + initial)
+  uint32_t act_count[3];      // [2]: movers this step
+  uint32_t wait_count[3];     // movers still waiting after each round (rotation)
   uint32_t bar_count;         // grid barrier arrivals
   uint32_t bar_gen;           // grid barrier generation
   int32_t rounds_last;        // movement rounds of the last step
@@ -63,6 +76,10 @@ struct Ctl {
   unsigned long long flagged;
   unsigned int max_dp_bits;          // float bits of max |p32 - p64|
   unsigned int pad1;
+  // movement instrumentation of the last step: agents still waiting after
+  // each round's claims, and the global timer at the start of each round
+  uint32_t round_n[kRoundLog];
+  unsigned long long round_ns[kRoundLog + 1];
 };
 
 struct Chunks {
@@ -79,8 +96,11 @@ struct StepArgs {
   int32_t* exited;       // [n_rep] agents that left through an exit, total
   uint32_t* queue;       // [q_cap] FP64 re-check queue (rep << 24 | slot)
   uint32_t q_cap;
-  uint32_t* act[3];      // movement work lists (rep << 24 | slot)
+  MoveEntry* act[3];     // [2]: movers of the step
+  uint32_t* act_info[3]; // [2]: per mover footprint length, exit flag, (dx, dy)
   uint32_t act_cap;
+  // movement state when a block's movers do not fit its shared memory
+  uint32_t *mv_prio, *mv_c0, *mv_ref, *mv_info, *mv_list[3];
   unsigned long long* dig_cell;  // [dig_cap * n_rep] per-step digests (optional)
   unsigned long long* dig_des;
   int32_t dig_cap;
@@ -124,5 +144,6 @@ int test_philox_launch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, 
                        cudaStream_t s);
 int test_ex2_launch(float lo, float hi, unsigned long long* out_max_rel_bits, cudaStream_t s);
 int test_barrier_timeout_launch(Ctl* ctl, int grid, cudaStream_t s);
+int test_barrier_cost_launch(Ctl* ctl, int grid, int block, int iters, cudaStream_t s);
 
 }  // namespace fastgb

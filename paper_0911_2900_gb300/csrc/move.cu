@@ -11,27 +11,53 @@
 //   cell held by an agent that stays this step, or the first exit cell.
 //   Agent i reads only cells of F_i (plus constant cells: stayers and exits)
 //   and writes only cells of F_i.  Two agents with disjoint footprints
-//   commute; so committing, in each round, every agent whose footprint
-//   touches no footprint of a lower-priority agent still waiting keeps every
-//   conflicting pair in priority order, which is equivalent to the serial
-//   loop.  Each round: P1 claims (64-bit atomicMin of the priority on every
-//   footprint cell), grid barrier, P2 check-and-commit, grid barrier.  The
-//   lowest-priority waiting agent always commits, so the loop ends after at
-//   most (number of movers) rounds; in practice the longest local priority
-//   chain.  Claims are cleared in the round after they were made (two claim
-//   arrays), so no extra barrier is needed.
+//   commute; so moving, in each round, every waiting agent whose footprint
+//   holds no claim of a lower-priority waiting agent keeps every conflicting
+//   pair in priority order, which is equivalent to the serial loop.
+//   Claims are 64-bit atomicMin of the priority on every footprint cell, in
+//   three arrays used in rotation: in round r every waiting agent checks its
+//   claims in array r%3 and either moves or claims again in array (r+1)%3;
+//   the claims of round r-1 are cleared in round r.  One grid barrier per
+//   round.  The lowest-priority waiting agent always moves, so the loop ends
+//   after at most (number of movers) rounds; in practice after the longest
+//   local priority chain.  Each block keeps its slice of the movers and its
+//   waiting lists in shared memory (in global memory when the slices are too
+//   large).
 #include "fast_device.cuh"
 
 namespace fastgb {
 
-constexpr uint32_t MV_LEN = 0x7u;        // footprint path length (0..5)
-constexpr uint32_t MV_EXIT = 0x8u;       // path ends on an exit cell
-constexpr uint32_t MV_DONE = 0x10u;      // committed
-constexpr uint32_t MV_GONE = 0x20u;      // left through an exit
-constexpr int MV_SFIN_SHIFT = 8;         // final step index along the path
+// info word of a work-list entry
+constexpr uint32_t MV_LEN = 0x7u;      // footprint path length (0..5)
+constexpr uint32_t MV_EXIT = 0x8u;     // the path reaches an exit cell after the footprint
+constexpr int MV_DX = 4;               // dx + 8, 4 bits
+constexpr int MV_DY = 8;               // dy + 8, 4 bits
+constexpr uint32_t MV_DONE = 0x1000u;  // moved
 
-__device__ __forceinline__ int path_cell(int x0, int y0, int dx, int dy, int L, int s, int W) {
-  return (y0 + div_half_away(s * dy, L)) * W + (x0 + div_half_away(s * dx, L));
+// Straight-path table for every offset (dx, dy) in [-5, 5]^2 and step
+// s = 1..5: (dx_s, dy_s) = (q(s*dx, L), q(s*dy, L)), L = max(|dx|, |dy|),
+// q = division rounded half away from zero.
+struct PathTab {
+  int8_t d[11 * 11 * 5][2];
+};
+
+__device__ __forceinline__ void build_path_tab(PathTab* t) {
+  for (int i = threadIdx.x; i < 121; i += blockDim.x) {
+    const int dx = i % 11 - 5, dy = i / 11 - 5;
+    const int L = max(abs(dx), abs(dy));
+    for (int s = 1; s <= 5; ++s) {
+      const bool ok = L > 0 && s <= L;
+      t->d[i * 5 + s - 1][0] = ok ? (int8_t)div_half_away(s * dx, L) : 0;
+      t->d[i * 5 + s - 1][1] = ok ? (int8_t)div_half_away(s * dy, L) : 0;
+    }
+  }
+}
+
+__device__ __forceinline__ int path_cell_tab(const PathTab* t, int c0, int W, uint32_t info, int s) {
+  if (s == 0) return c0;
+  const int dx = (int)((info >> MV_DX) & 0xF) - 8, dy = (int)((info >> MV_DY) & 0xF) - 8;
+  const int i = ((dy + 5) * 11 + (dx + 5)) * 5 + s - 1;
+  return c0 + (int)t->d[i][1] * W + (int)t->d[i][0];
 }
 
 // ---------------------------------------------------------------------------
@@ -55,11 +81,19 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
     const int x0 = cell % W, y0 = cell / W;
     const int dx = des % W - x0, dy = des / W - y0;
     const int L = max(abs(dx), abs(dy));
+    // all path records first (independent loads), then the scan
+    uint32_t pr[5];
+#pragma unroll
+    for (int s = 1; s <= 5; ++s)
+      pr[s - 1] = (s <= L) ? R.rec[(y0 + div_half_away(s * dy, L)) * W +
+                                   (x0 + div_half_away(s * dx, L))]
+                           : REC_STA;
     int fp = 0;
     uint32_t ex = 0;
-    for (int s = 1; s <= L; ++s) {
-      const uint32_t r = R.rec[path_cell(x0, y0, dx, dy, L, s, W)];
-      if (r & REC_STA) break;
+#pragma unroll
+    for (int s = 1; s <= 5; ++s) {
+      const uint32_t r = pr[s - 1];
+      if (s > L || (r & REC_STA)) break;
       if (rec_exit(r)) {
         ex = MV_EXIT;
         break;
@@ -67,10 +101,17 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
       fp = s;
     }
     if (fp == 0 && !ex) continue;
-    R.prio[slot] = move_priority((uint32_t)R.id[slot], (uint32_t)t, R.seed_lo, R.seed_hi);
-    R.mvinfo[slot] = (uint32_t)fp | ex;
-    const uint32_t i = atomicAdd(&a.ctl->act_count[2], 1u);
-    if (i < a.act_cap) a.act[2][i] = ((uint32_t)rep << 24) | (uint32_t)slot;
+    const uint32_t i = append_slot(&a.ctl->act_count[2]);
+    if (i < a.act_cap) {
+      uint32_t k0, k1;
+      move_step_key((uint32_t)t, R.seed_lo, R.seed_hi, &k0, &k1);
+      MoveEntry e;
+      e.c0 = (uint32_t)cell;
+      e.ref = ((uint32_t)rep << 24) | (uint32_t)slot;
+      e.prio = move_priority((uint32_t)R.id[slot], k0, k1);
+      e.info = (uint32_t)fp | ex | ((uint32_t)(dx + 8) << MV_DX) | ((uint32_t)(dy + 8) << MV_DY);
+      a.act[2][i] = e;
+    }
   }
   // agents alive at the start of the step
   for (int o = 16; o > 0; o >>= 1) alive_local += __shfl_xor_sync(0xffffffffu, alive_local, o);
@@ -80,7 +121,7 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
 
 // ---------------------------------------------------------------------------
 // Grid-wide barrier for a cooperative launch, with a time limit: a block that
-// waits longer than ctl->barrier_ns_limit records FAST timeout in ctl->err and
+// waits longer than ctl->barrier_ns_limit records the timeout in ctl->err and
 // every block then leaves the kernel at its next barrier.
 __device__ bool grid_barrier(Ctl* ctl) {
   __shared__ int s_ok;
@@ -109,7 +150,7 @@ __device__ bool grid_barrier(Ctl* ctl) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -120,151 +161,237 @@ __device__ bool grid_barrier(Ctl* ctl) {
   return s_ok != 0;
 }
 
-struct Foot {
-  int x0, y0, dx, dy, L, n, W;
-  int c0;
-};
-
-__device__ __forceinline__ Foot footprint(const RepDev& R, int slot, uint32_t info) {
-  Foot f;
-  f.W = R.W;
-  f.c0 = R.cell[slot];
-  const int des = R.desired[slot];
-  f.x0 = f.c0 % f.W;
-  f.y0 = f.c0 / f.W;
-  f.dx = des % f.W - f.x0;
-  f.dy = des / f.W - f.y0;
-  f.L = max(abs(f.dx), abs(f.dy));
-  f.n = (int)(info & MV_LEN);
-  return f;
+__device__ __forceinline__ bool round_barrier(Ctl* ctl, bool single) {
+  if (single) {
+    __threadfence_block();
+    __syncthreads();
+    return true;
+  }
+  return grid_barrier(ctl);
 }
 
-__device__ __forceinline__ int foot_cell(const Foot& f, int s) {
-  return s == 0 ? f.c0 : path_cell(f.x0, f.y0, f.dx, f.dy, f.L, s, f.W);
+__device__ __forceinline__ void foot_cells(const PathTab* tab, uint32_t c0, int W, uint32_t info,
+                                           int* c) {
+#pragma unroll
+  for (int s = 0; s < 6; ++s) c[s] = path_cell_tab(tab, (int)c0, W, info, s);
 }
 
-__global__ void __launch_bounds__(256) k_move_rounds(StepArgs a) {
+// Path records an agent may walk: path cells 1..min(L, n + 1), where past
+// the footprint only one more cell can be reached, and it is constant (a
+// stayer, which blocks, or the exit the agent leaves by).
+__device__ __forceinline__ int walk_len(uint32_t info) {
+  const int n = (int)(info & MV_LEN);
+  const int dx = (int)((info >> MV_DX) & 0xF) - 8, dy = (int)((info >> MV_DY) & 0xF) - 8;
+  return min(max(abs(dx), abs(dy)), n + 1);
+}
+
+// Moves one agent that owns its footprint, given the records of its start
+// cell (pr[0]) and path cells (pr[s] for cell s; blocked past the walk
+// length), all read after the last barrier.  The agent owns every cell it
+// writes, so the records it read are still current.
+__device__ __forceinline__ void commit_move(const StepArgs& a, const RepDev& R, int rep, int slot,
+                                            const int* c, const uint32_t* pr) {
+  int cfin = c[0];
+  uint32_t rfin = pr[0];
+  bool gone = false, stop = false;
+#pragma unroll
+  for (int s = 1; s <= 5; ++s) {
+    const uint32_t rr = pr[s];
+    stop = stop || (rr & REC_OCC);
+    if (!stop) {
+      cfin = c[s];
+      rfin = rr;
+      if (rec_exit(rr)) {
+        gone = true;
+        stop = true;
+      }
+    }
+  }
+  if (cfin == c[0]) return;
+  __stcg(&R.rec[c[0]], pr[0] & ~(REC_OCC | REC_STA));
+  if (!gone) {
+    __stcg(&R.rec[cfin], rfin | REC_OCC);
+    R.cell[slot] = cfin;
+  } else {
+    R.cell[slot] = -1;
+    atomicAdd(&a.exited[rep], 1);
+  }
+}
+
+__global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
+  extern __shared__ __align__(16) unsigned char dsm[];
+  __shared__ PathTab tab;
+  __shared__ uint32_t s_cnt[3];
+  build_path_tab(&tab);
   Ctl* ctl = a.ctl;
-  const uint32_t gtid = blockIdx.x * blockDim.x + threadIdx.x;
-  const uint32_t gsz = gridDim.x * blockDim.x;
   const uint32_t n0 = min(__ldcg(&ctl->act_count[2]), a.act_cap);
-  const uint32_t* in = a.act[2];
-  uint32_t n_in = n0;
+  const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
+  const uint32_t start = (uint32_t)(((unsigned long long)n0 * b) / G);
+  const uint32_t nb = (uint32_t)(((unsigned long long)n0 * (b + 1)) / G) - start;
+  const bool in_smem = (n0 + G - 1) / G <= (uint32_t)kMoveSmemCap;  // same for every block
+  uint32_t *P, *C0, *RF, *IN, *L[3];
+  if (in_smem) {
+    P = reinterpret_cast<uint32_t*>(dsm);
+    C0 = P + kMoveSmemCap;
+    RF = C0 + kMoveSmemCap;
+    IN = RF + kMoveSmemCap;
+    L[0] = IN + kMoveSmemCap;
+    L[1] = L[0] + kMoveSmemCap;
+    L[2] = L[1] + kMoveSmemCap;
+  } else {
+    P = a.mv_prio + start;
+    C0 = a.mv_c0 + start;
+    RF = a.mv_ref + start;
+    IN = a.mv_info + start;
+    for (int j = 0; j < 3; ++j) L[j] = a.mv_list[j] + start;
+  }
+  if (tid < 3) s_cnt[tid] = 0u;
+  if (b == 0 && tid == 0) ctl->round_ns[0] = global_ns();
+  __syncthreads();
+  // this block's movers, and their claims for round 0
+  for (uint32_t k = tid; k < nb; k += blockDim.x) {
+    const MoveEntry e = a.act[2][start + k];
+    const uint32_t info = e.info;
+    P[k] = e.prio;
+    C0[k] = e.c0;
+    RF[k] = e.ref;
+    IN[k] = info;
+    L[0][k] = k;
+    const RepDev& R = a.reps[e.ref >> 24];
+    int c[6];
+    foot_cells(&tab, e.c0, R.W, info, c);
+    const int n = (int)(info & MV_LEN);
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+      if (s <= n) atomicMin(&R.claim[0][c[s]], e.prio);
+  }
+  if (tid == 0) s_cnt[0] = nb;
+  if (!grid_barrier(ctl)) return;
   int r = 0;
-  bool ok = true;
   for (;;) {
-    uint32_t* out = a.act[r & 1];
-    uint32_t* out_cnt = &ctl->act_count[r & 1];
-    // P1: clear last round's claims, claim this round's footprints
-    for (uint32_t i = gtid; i < n_in; i += gsz) {
-      const uint32_t e = in[i];
-      const int rep = (int)(e >> 24), slot = (int)(e & 0xFFFFFFu);
+    // round r walks the list of round r-1 (a superset of the agents still
+    // waiting): clear their claims of round r-1; each waiting one checks its
+    // claims of round r, moves or claims for round r+1
+    const int it = r == 0 ? 0 : (r - 1) % 3;
+    const int ap = (r + 1) % 3;
+    if (b == 0 && tid == 0) ctl->wait_count[(r + 2) % 3] = 0u;
+    const uint32_t n_it = s_cnt[it];
+    __syncthreads();
+    if (tid == 0) s_cnt[ap] = 0u;
+    __syncthreads();
+    for (uint32_t k = tid; k < n_it; k += blockDim.x) {
+      const uint32_t idx = L[it][k];
+      const uint32_t info = IN[idx];
+      const uint32_t ref = RF[idx];
+      const uint32_t p = P[idx];
+      const int rep = (int)(ref >> 24), slot = (int)(ref & 0xFFFFFFu);
       const RepDev& R = a.reps[rep];
-      const uint32_t info = __ldcg(&R.mvinfo[slot]);
-      const Foot f = footprint(R, slot, info);
+      int c[6];
+      foot_cells(&tab, C0[idx], R.W, info, c);
+      const int n = (int)(info & MV_LEN);
       if (r > 0) {
-        unsigned long long* old = R.claim[(r - 1) & 1];
-        for (int s = 0; s <= f.n; ++s) __stcg(&old[foot_cell(f, s)], ~0ull);
+        uint32_t* old = R.claim[(r - 1) % 3];
+#pragma unroll
+        for (int s = 0; s < 6; ++s)
+          if (s <= n) __stcg(&old[c[s]], 0xFFFFFFFFu);
       }
-      if (!(info & MV_DONE)) {
-        unsigned long long* now = R.claim[r & 1];
-        const unsigned long long p = R.prio[slot];
-        for (int s = 0; s <= f.n; ++s) atomicMin(&now[foot_cell(f, s)], p);
-        const uint32_t j = atomicAdd(out_cnt, 1u);
-        out[j] = e;
-      }
-    }
-    if (!(ok = grid_barrier(ctl))) break;
-    const uint32_t n_out = __ldcg(out_cnt);
-    if (n_out == 0) break;
-    if (r + 1 > (int)n0 + 1) {
-      if (gtid == 0) atomicCAS(&ctl->err, 0, kDevErrRounds);
-      ok = false;
-      break;
-    }
-    if (gtid == 0) ctl->act_count[(r + 1) & 1] = 0u;  // next round's output counter
-    // P2: commit the agents that own all their footprint cells
-    for (uint32_t i = gtid; i < n_out; i += gsz) {
-      const uint32_t e = out[i];
-      const int rep = (int)(e >> 24), slot = (int)(e & 0xFFFFFFu);
-      const RepDev& R = a.reps[rep];
-      const uint32_t info = __ldcg(&R.mvinfo[slot]);
-      const Foot f = footprint(R, slot, info);
-      const unsigned long long p = R.prio[slot];
-      const unsigned long long* now = R.claim[r & 1];
+      if (info & MV_DONE) continue;
+      // the claims of the round and the path records, in one round trip
+      const uint32_t* now = R.claim[r % 3];
+      const int wl = walk_len(info);
+      uint32_t cl[6];
+      uint32_t pr[6];
+#pragma unroll
+      for (int s = 0; s < 6; ++s) cl[s] = (s <= n) ? __ldcg(&now[c[s]]) : p;
+#pragma unroll
+      for (int s = 0; s < 6; ++s) pr[s] = (s <= wl) ? __ldcg(&R.rec[c[s]]) : REC_OCC;
       bool mine = true;
-      for (int s = 0; s <= f.n; ++s) mine = mine && (__ldcg(&now[foot_cell(f, s)]) == p);
-      if (!mine) continue;
-      // walk the path against the current occupancy
-      int sfin = 0;
-      bool gone = false;
-      for (int s = 1; s <= f.L; ++s) {
-        const int nc = foot_cell(f, s);
-        const uint32_t rr = __ldcg(&R.rec[nc]);
-        if (rr & REC_OCC) break;
-        sfin = s;
-        if (rec_exit(rr)) {
-          gone = true;
-          break;
-        }
+#pragma unroll
+      for (int s = 0; s < 6; ++s) mine &= (cl[s] == p);
+      if (mine) {
+        commit_move(a, R, rep, slot, c, pr);
+        IN[idx] = info | MV_DONE;
+      } else {
+        uint32_t* nxt = R.claim[ap];
+#pragma unroll
+        for (int s = 0; s < 6; ++s)
+          if (s <= n) atomicMin(&nxt[c[s]], p);
+        L[ap][append_slot(&s_cnt[ap])] = idx;
       }
-      if (sfin > 0) {
-        const uint32_t r0 = __ldcg(&R.rec[f.c0]);
-        __stcg(&R.rec[f.c0], r0 & ~(REC_OCC | REC_STA));
-        if (!gone) {
-          const int fc = foot_cell(f, sfin);
-          const uint32_t r1 = __ldcg(&R.rec[fc]);
-          __stcg(&R.rec[fc], r1 | REC_OCC);
-        }
-      }
-      __stcg(&R.mvinfo[slot],
-             info | MV_DONE | (gone ? MV_GONE : 0u) | ((uint32_t)sfin << MV_SFIN_SHIFT));
     }
-    if (!(ok = grid_barrier(ctl))) break;
-    in = out;
-    n_in = n_out;
+    __syncthreads();
+    if (tid == 0 && s_cnt[ap]) atomicAdd(&ctl->wait_count[ap], s_cnt[ap]);
+    if (!grid_barrier(ctl)) return;
+    const uint32_t waiting = __ldcg(&ctl->wait_count[ap]);
+    if (b == 0 && tid == 0 && r < kRoundLog) {
+      ctl->round_n[r] = waiting;
+      ctl->round_ns[r + 1] = global_ns();
+    }
     ++r;
-  }
-  if (!ok) return;
-  // final positions
-  for (uint32_t i = gtid; i < n0; i += gsz) {
-    const uint32_t e = a.act[2][i];
-    const int rep = (int)(e >> 24), slot = (int)(e & 0xFFFFFFu);
-    const RepDev& R = a.reps[rep];
-    const uint32_t info = __ldcg(&R.mvinfo[slot]);
-    const int sfin = (int)(info >> MV_SFIN_SHIFT) & 0xF;
-    if (info & MV_GONE) {
-      R.cell[slot] = -1;
-      atomicAdd(&a.exited[rep], 1);
-    } else if (sfin > 0) {
-      const Foot f = footprint(R, slot, info);
-      R.cell[slot] = foot_cell(f, sfin);
+    if (waiting == 0) break;
+    if (r > (int)n0 + 1) {
+      if (b == 0 && tid == 0) atomicCAS(&ctl->err, 0, kDevErrRounds);
+      return;
     }
   }
-  if (gtid == 0) {
+  // the agents of the last round all moved: clear their claims
+  const int last = (r - 1) % 3;
+  for (uint32_t k = tid; k < s_cnt[last]; k += blockDim.x) {
+    const uint32_t idx = L[last][k];
+    const RepDev& R = a.reps[RF[idx] >> 24];
+    int c[6];
+    foot_cells(&tab, C0[idx], R.W, IN[idx], c);
+    const int n = (int)(IN[idx] & MV_LEN);
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+      if (s <= n) __stcg(&R.claim[last][c[s]], 0xFFFFFFFFu);
+  }
+  if (b == 0 && tid == 0) {
     ctl->rounds_last = r;
     ctl->rounds_total += (unsigned long long)r;
     if (r > ctl->rounds_max) ctl->rounds_max = r;
   }
 }
 
+// Cost of the grid barrier: `iters` barriers in a row, block 0 thread 0
+// records the elapsed global time in ctl->round_ns[0].
+__global__ void __launch_bounds__(1024, 1) k_barrier_cost(Ctl* ctl, int iters) {
+  const unsigned long long t0 = global_ns();
+  for (int i = 0; i < iters; ++i)
+    if (!grid_barrier(ctl)) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) ctl->round_ns[0] = global_ns() - t0;
+}
+
+int test_barrier_cost_launch(Ctl* ctl, int grid, int block, int iters, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_barrier_cost, ctl, iters) == cudaSuccess ? 0 : -1;
+}
+
 // ---------------------------------------------------------------------------
-__global__ void k_step_begin(StepArgs a) {
-  if (threadIdx.x == 0) {
-    a.ctl->q_count = 0u;
-    a.ctl->act_count[0] = 0u;
-    a.ctl->act_count[1] = 0u;
-    a.ctl->act_count[2] = 0u;
+__device__ __forceinline__ void reset_step_counters(Ctl* c) {
+  c->q_count = 0u;
+  for (int i = 0; i < 3; ++i) {
+    c->act_count[i] = 0u;
+    c->wait_count[i] = 0u;
   }
+}
+
+__global__ void k_step_begin(StepArgs a) {
+  if (threadIdx.x == 0) reset_step_counters(a.ctl);
 }
 
 __global__ void k_step_end(StepArgs a) {
   if (threadIdx.x == 0) {
     a.ctl->t += 1;
-    a.ctl->q_count = 0u;
-    a.ctl->act_count[0] = 0u;
-    a.ctl->act_count[1] = 0u;
-    a.ctl->act_count[2] = 0u;
+    reset_step_counters(a.ctl);
   }
 }
 
@@ -274,11 +401,17 @@ int move_prep_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t
   return 0;
 }
 
+size_t move_rounds_smem() { return (size_t)kMoveSmemCap * 28; }
+
 int move_rounds_max_grid(int block, int* grid_out) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -1;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return -1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_move_rounds, block, 0) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_move_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)move_rounds_smem()) != cudaSuccess)
+    return -1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_move_rounds, block,
+                                                    move_rounds_smem()) != cudaSuccess)
     return -1;
   *grid_out = sms * (per > 0 ? per : 1);
   return 0;
@@ -288,7 +421,7 @@ int move_rounds_launch(const StepArgs& a, int grid, int block, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = move_rounds_smem();
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

@@ -111,24 +111,30 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
       if (slot >= end) continue;
       const int cell = R.cell[slot];
       if (cell < 0) continue;
+      const int id = R.id[slot];
       const uint32_t rec0 = rec[cell];
-      const int a0 = rec_a(rec0), b0 = rec_b(rec0);
       const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
       const unsigned long long m1 = (K > 64) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
-
+      // all candidate records first (independent loads in flight together),
+      // then the weights; an inadmissible candidate reads as blocked
+      uint32_t rr[Q];
+#pragma unroll
+      for (int j = 0; j < Q; ++j) {
+        const int k = sub * Q + j;
+        const bool adm = (k < K) && (k != CENTER) && mask_bit(m0, m1, k);
+        rr[j] = adm ? rec[cell + s_off[k]] : REC_OCC;
+      }
+      const int a0 = rec_a(rec0), b0 = rec_b(rec0);
       float w[Q];
       float lsum = 0.f;
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
         const int k = sub * Q + j;
         float wk = 0.f;
-        if (k < K && mask_bit(m0, m1, k)) {
-          if (k == CENTER) {
-            wk = 1.0f;
-          } else {
-            const uint32_t r = rec[cell + s_off[k]];
-            if (!(r & REC_OCC)) wk = ex2_approx(ds32(rec_a(r) - a0, rec_b(r) - b0) * c32);
-          }
+        if (k == CENTER) {
+          wk = 1.0f;
+        } else if (!(rr[j] & REC_OCC)) {
+          wk = ex2_approx(ds32(rec_a(rr[j]) - a0, rec_b(rr[j]) - b0) * c32);
         }
         w[j] = wk;
         lsum += wk;
@@ -143,7 +149,6 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
       float excl = __shfl_up_sync(gmask, incl, 1, G);
       if (sub == 0) excl = 0.f;
       const float Wt = __shfl_sync(gmask, incl, G - 1, G);
-      const int id = R.id[slot];
       float uf = 0.f;
       if (sub == 0) uf = (float)plan_uniform((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
       uf = __shfl_sync(gmask, uf, 0, G);
@@ -207,7 +212,7 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
           R.desired[slot] = target;
           set_static(rec, cell, rec0, target == cell);
         } else {
-          const uint32_t qi = atomicAdd(&a.ctl->q_count, 1u);
+          const uint32_t qi = append_slot(&a.ctl->q_count);
           if (qi < a.q_cap) a.queue[qi] = ((uint32_t)rep << 24) | (uint32_t)slot;
         }
       }

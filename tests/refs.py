@@ -33,10 +33,19 @@ def uniform53(seed, agent_id, t):
     return ((r[0] >> 5) * 2 ** 26 + (r[1] >> 6)) / 2.0 ** 53
 
 
+def fmix32(h):
+    """MurmurHash3 32-bit finalizer (A. Appleby)."""
+    h ^= h >> 16
+    h = (h * 0x85EBCA6B) & M32
+    h ^= h >> 13
+    h = (h * 0xC2B2AE35) & M32
+    h ^= h >> 16
+    return h
+
+
 def move_priority(seed, agent_id, t):
-    r = philox4x32_10([agent_id, t, 1, 0], [seed & M32, seed >> 32])
-    k64 = (r[0] << 32) | r[1]
-    return ((k64 >> 24) << 24) | agent_id
+    k = philox4x32_10([0, t, 2, 0], [seed & M32, seed >> 32])
+    return fmix32(fmix32(agent_id ^ k[0]) ^ k[1])
 
 
 def reach_offsets(v, metric="l2"):

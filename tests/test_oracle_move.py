@@ -63,6 +63,24 @@ def test_priority_matches_reference(orc):
                 assert orc.move_priority(seed, i, t) == refs.move_priority(seed, i, t)
 
 
+def test_priority_is_a_random_permutation(orc):
+    """Each step orders the agents by a bijection of their ids (no ties), and
+    the order of two given agents is a fair coin over the steps."""
+    ids = np.arange(5000, dtype=np.int64)
+    for t in (0, 7):
+        p = np.array([refs.move_priority(3, int(i), t) for i in ids])
+        assert len(np.unique(p)) == len(p)
+    wins = sum(refs.move_priority(5, 10, t) < refs.move_priority(5, 11, t) for t in range(4000))
+    assert abs(wins - 2000) < 4 * np.sqrt(1000)       # binomial(4000, 1/2): 4 sigma
+    # agent 0 lands uniformly in the order of 64 agents
+    ranks = np.zeros(64)
+    for t in range(6400):
+        p = [refs.move_priority(9, i, t) for i in range(64)]
+        ranks[sorted(range(64), key=lambda i: p[i]).index(0)] += 1
+    from scipy import stats
+    assert stats.chisquare(ranks).pvalue > 1e-3
+
+
 def _check_invariants(sim, n0, exited):
     occ = sim.occ
     alive = sim.cell >= 0
