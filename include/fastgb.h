@@ -183,6 +183,26 @@ int fast_precision_report_run(fast_ctx* ctx, fast_precision_report* out);
  * reads (own cells and line-of-sight reach offsets), for byte accounting. */
 int fast_reach_union(fast_ctx* ctx, int32_t replicate, int64_t* cells);
 
+/* Planning pass that allocates no device memory (no counterpart in the
+ * paper: it exists for callers that cannot allocate when they plan, such as
+ * code capturing a CUDA graph on its stream, or a process whose device memory
+ * is all held by another allocator).  It writes, for each agent of the
+ * replicate present in the context with id < id_bound, the desired cell of
+ * step `step` into desired_by_id_dev[id] (a device buffer the caller owns;
+ * other entries are left as they are), computed exactly like a planning pass
+ * of the context (FP32 weights, FP64 re-check inside the margin).  The
+ * context's state is read, never changed, and the call only queues work on
+ * the context's stream.  Its scratch is one fixed array of 4 MiB + 256 bytes
+ * inside the library, held on every device that loads the library until the
+ * process exits: hence at most 2^20 agent slots per replicate (FAST_EINVAL
+ * beyond).  Every call on a device shares that array, so calls that can
+ * overlap on the GPU race; order them on one stream.  The first call on a
+ * device looks up the array's device address (make it before any stream
+ * capture).  FAST_ESTATE if the context has not run fast_step or
+ * fast_plan_only since its last fast_init_grid / fast_place_agents. */
+int fast_plan_noalloc(fast_ctx* ctx, int32_t replicate, int32_t step, int32_t id_bound,
+                      int32_t* desired_by_id_dev);
+
 int fast_set_option(fast_ctx* ctx, int32_t option, int64_t value);
 const char* fast_last_error(const fast_ctx* ctx);
 void fast_destroy(fast_ctx* ctx);

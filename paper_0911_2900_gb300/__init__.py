@@ -79,6 +79,7 @@ EXPORTS = {
     "fast_move_profile": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "fast_reach_union": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fast_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "fast_plan_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "fast_last_error": (C.c_char_p, [C.c_void_p]),
     "fast_destroy": (None, [C.c_void_p]),
     "fast_selftest_exp64": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
@@ -255,6 +256,13 @@ class Context:
         v = C.c_int64()
         self._check(self.lib.fast_reach_union(self.h, rep, C.byref(v)), "fast_reach_union")
         return v.value
+
+    def plan_noalloc(self, rep: int, step: int, out_by_id) -> None:
+        """Allocation-free planning pass into `out_by_id` (a CUDA int32 tensor,
+        indexed by agent id); queued on the context's stream."""
+        self._check(self.lib.fast_plan_noalloc(self.h, rep, int(step), int(out_by_id.numel()),
+                                               C.c_void_p(out_by_id.data_ptr())),
+                    "fast_plan_noalloc")
 
     def set_option(self, name: str, value: int):
         self._check(self.lib.fast_set_option(self.h, OPT[name], int(value)), "fast_set_option")

@@ -964,6 +964,29 @@ int fast_reach_union(fast_ctx* c, int32_t r, int64_t* cells) {
   return FAST_OK;
 }
 
+// Planning pass into a caller buffer without any device allocation: see
+// noalloc.cu.  Reads the context's state, never changes it, never
+// synchronises; the only scratch is the library's fixed re-check queue.
+int fast_plan_noalloc(fast_ctx* c, int32_t r, int32_t step, int32_t id_bound,
+                      int32_t* desired_by_id_dev) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (!rep_ok(c, r) || step < 0 || id_bound < 0 || (id_bound > 0 && !desired_by_id_dev))
+    return fail(c, FAST_EINVAL, "bad replicate, step, id_bound or output pointer");
+  RepHost& R = c->reps[r];
+  if (!R.placed) return fail(c, FAST_ESTATE, "replicate %d has no agents", r);
+  if (c->layout_dirty)
+    return fail(c, FAST_ESTATE, "layout not built yet: run fast_step or fast_plan_only once first");
+  if (R.cap > noalloc_max_agents())
+    return fail(c, FAST_EINVAL, "replicate %d has %d agent slots; this pass holds at most %d", r,
+                R.cap, noalloc_max_agents());
+  const int rc = noalloc_plan_launch(R.d, R.cap, step, desired_by_id_dev, id_bound, c->sms,
+                                     c->stream);
+  if (rc == -1) return fail(c, FAST_ECUDA, "address of the fixed re-check queue unavailable");
+  if (rc != 0) return fail(c, FAST_ECUDA, "launch of the allocation-free planning pass failed");
+  return FAST_OK;
+}
+
 int fast_set_option(fast_ctx* c, int32_t option, int64_t value) {
   if (!c) return FAST_EINVAL;
   if (c->poisoned) return FAST_ESTATE;
