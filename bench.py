@@ -375,7 +375,9 @@ def bench_ours(args):
             "move_rounds_per_step": (st1["move_rounds"] - st0["move_rounds"]) / args.steps,
             "move_last_step": {"waiting_after_round": [int(x) for x in mv_wait[:12]],
                                "round_us": [round(float(x), 2) for x in mv_us[:12]],
-                               "rounds": int(len(mv_wait))},
+                               "rounds": int(len(mv_wait)),
+                               "phases_max_over_blocks": [round(float(x) / 1e3, 2) if i not in (4, 5) else int(x)
+                                                          for i, x in enumerate(ctx.last_move_phases)]},
             "roofline": {"bound": "hbm", "kernel": "k_plan_fp32", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_kind": peak_kind,

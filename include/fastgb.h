@@ -171,7 +171,11 @@ int fast_phase_times(fast_ctx* ctx, float* ms4);
 /* Movement rounds of the last step (waits for the stream): n_wait[r] = agents
  * still waiting after round r's claims, t_ns[r] = device global timer at the
  * start of round r (t_ns has one entry more).  Writes min(max_rounds, 64)
- * rounds; returns the number of rounds of the step or a negative error. */
+ * rounds; returns the number of rounds of the step or a negative error.
+ * With max_rounds >= 73, t_ns[65..72] also receive per-phase maxima over the
+ * blocks (ns; load of the movers and first claims, the same plus the grid
+ * barrier, the work of rounds 0 and 1, and the movers per block in rounds 0
+ * and 1 as counts). */
 int fast_move_profile(fast_ctx* ctx, int32_t max_rounds, uint32_t* n_wait, uint64_t* t_ns);
 
 /* Runs the FP32 planning of the current state without re-check next to the

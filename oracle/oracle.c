@@ -357,13 +357,14 @@ void orc_plan_all(const orc_world* w, const int32_t* occ, int32_t n, const int32
 
 /* ------------------------------------------------------------------------- */
 /* Movement order (reading R7): a fresh pseudo-random permutation of the
- * agents every step.  The step key (k0, k1) is the first two words of
- * Philox(key = seed, ctr = (0, t, 2, 0)); agent id gets the priority
- *   pi_t(id) = fmix32(fmix32(id ^ k0) ^ k1)
- * with fmix32 the finalizer of MurmurHash3 (A. Appleby): xor-shifts and
- * multiplications by odd constants, each a bijection of the 32-bit words, so
- * pi_t is a bijection and no two agents share a priority.  Agents move in
- * ascending priority. */
+ * agents every step, as a keyed permutation of the 24-bit agent ids.  The
+ * step keys k0..k3 are the four words of Philox(key = seed, ctr =
+ * (0, t, 2, 0)); the id is split into 12-bit halves (L, R) and passed through
+ * a four-round Feistel network (Luby and Rackoff, 1988)
+ *   (L, R) <- (R, L ^ (fmix32(R ^ k_i) & 0xFFF)),  i = 0..3,
+ * fmix32 being the finalizer of MurmurHash3 (A. Appleby).  Every Feistel
+ * round is invertible, so pi_t is a permutation of [0, 2^24) and no two agents
+ * share a priority.  Agents move in ascending pi_t(id). */
 static uint32_t orc_fmix32(uint32_t h) {
   h ^= h >> 16;
   h *= 0x85EBCA6Bu;
@@ -373,19 +374,27 @@ static uint32_t orc_fmix32(uint32_t h) {
   return h;
 }
 
-static void orc_step_key(uint64_t seed, int32_t t, uint32_t* k0, uint32_t* k1) {
+static void orc_step_keys(uint64_t seed, int32_t t, uint32_t k[4]) {
   uint32_t ctr[4] = {0u, (uint32_t)t, 2u, 0u};
   uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
-  uint32_t rnd[4];
-  orc_philox4x32_10(ctr, key, rnd);
-  *k0 = rnd[0];
-  *k1 = rnd[1];
+  orc_philox4x32_10(ctr, key, k);
+}
+
+static uint32_t orc_feistel24(uint32_t id, const uint32_t k[4]) {
+  uint32_t L = (id >> 12) & 0xFFFu, R = id & 0xFFFu;
+  for (int i = 0; i < 4; ++i) {
+    uint32_t nl = R;
+    uint32_t nr = L ^ (orc_fmix32(R ^ k[i]) & 0xFFFu);
+    L = nl;
+    R = nr;
+  }
+  return (L << 12) | R;
 }
 
 uint32_t orc_move_priority(uint64_t seed, int32_t id, int32_t t) {
-  uint32_t k0, k1;
-  orc_step_key(seed, t, &k0, &k1);
-  return orc_fmix32(orc_fmix32((uint32_t)id ^ k0) ^ k1);
+  uint32_t k[4];
+  orc_step_keys(seed, t, k);
+  return orc_feistel24((uint32_t)id, k);
 }
 
 typedef struct {
@@ -407,11 +416,11 @@ int32_t orc_move(const orc_world* w, int32_t* occ, int32_t n, const int32_t* id,
                  const int32_t* desired, int32_t t) {
   orc_pi* order = (orc_pi*)malloc((size_t)(n > 0 ? n : 1) * sizeof(orc_pi));
   int32_t m = 0;
-  uint32_t k0, k1;
-  orc_step_key(w->seed, t, &k0, &k1);
+  uint32_t k[4];
+  orc_step_keys(w->seed, t, k);
   for (int32_t i = 0; i < n; ++i)
     if (cell[i] >= 0) {
-      order[m].p = orc_fmix32(orc_fmix32((uint32_t)id[i] ^ k0) ^ k1);
+      order[m].p = orc_feistel24((uint32_t)id[i], k);
       order[m].i = i;
       ++m;
     }

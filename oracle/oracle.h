@@ -76,7 +76,7 @@ void orc_plan_all(const orc_world* w, const int32_t* occ, int32_t n,
                   int32_t* desired, int32_t threads);
 
 /* Movement priority of agent id at step t (smaller moves earlier; a
- * bijection of the id for each step). */
+ * permutation of the 24-bit ids for each step). */
 uint32_t orc_move_priority(uint64_t seed, int32_t id, int32_t t);
 
 /* Sequential movement of all agents in priority order.  Updates cell (-1 when

@@ -584,7 +584,7 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   for (auto& p : R.d.claim) dfree(c, p);
   R.d.rec = nullptr;
   R.d.mask = nullptr;
-  R.d.claim[0] = R.d.claim[1] = R.d.claim[2] = nullptr;
+  R.d.claim[0] = R.d.claim[1] = nullptr;
   R.W = g->width;
   R.H = g->height;
   R.v = g->v_m;
@@ -594,8 +594,9 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   R.mw = R.K > 64 ? 2 : 1;
   if (int e = alloc_into(c, &R.d.rec, C)) return e;
   if (int e = alloc_into(c, &R.d.mask, C * R.mw)) return e;
+  const int64_t claim_cells = (int64_t)((R.W + 15) / 16) * ((R.H + 15) / 16) * 256;
   for (auto& p : R.d.claim)
-    if (int e = alloc_into(c, &p, C)) return e;
+    if (int e = alloc_into(c, &p, claim_cells)) return e;
   RepDev& d = R.d;
   d.W = R.W;
   d.H = R.H;
@@ -609,7 +610,8 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   d.seed_lo = (uint32_t)R.seed;
   d.seed_hi = (uint32_t)(R.seed >> 32);
   CUDA_TRY(c, cudaMemcpyAsync(d.rec, rec.data(), C * 4, cudaMemcpyHostToDevice, c->stream));
-  for (auto p : d.claim) CUDA_TRY(c, cudaMemsetAsync(p, 0xFF, C * 4, c->stream));
+  d.claim_tx = (R.W + 15) / 16;
+  for (auto p : d.claim) CUDA_TRY(c, cudaMemsetAsync(p, 0xFF, claim_cells * 4, c->stream));
   R.grid_set = true;
   R.placed = false;
   R.n = 0;
@@ -870,6 +872,8 @@ int fast_move_profile(fast_ctx* c, int32_t max_rounds, uint32_t* n_wait, uint64_
     if (t_ns) t_ns[i] = h.round_ns[i];
   }
   if (t_ns && n > 0) t_ns[n] = h.round_ns[n];
+  if (t_ns && max_rounds >= 64 + 1 + 8)
+    for (int i = 0; i < 8; ++i) t_ns[65 + i] = h.phase_ns[i];
   return h.rounds_last;
 }
 

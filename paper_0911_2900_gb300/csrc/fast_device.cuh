@@ -102,11 +102,12 @@ __device__ __forceinline__ double plan_uniform(uint32_t id, uint32_t t, uint32_t
   return __dmul_rn(__dadd_rn(__dmul_rn(hi, 67108864.0), lo), 0x1p-53);
 }
 
-// Movement order of step t: a keyed bijection of the agent id.  The step
-// key is the first two words of Philox(seed; (0, t, 2, 0)); the priority is
-// fmix32(fmix32(id ^ k0) ^ k1), fmix32 being MurmurHash3's finalizer (xor
-// shifts and odd multiplications, each invertible), so no two agents of a
-// replicate share a priority.  Smaller priorities move earlier.
+// Movement order of step t: a keyed permutation of the 24-bit agent ids.
+// The step keys are the four words of Philox(seed; (0, t, 2, 0)); the id's
+// 12-bit halves (L, R) pass through four Feistel rounds
+// (L, R) <- (R, L ^ (fmix32(R ^ k_i) & 0xFFF)), fmix32 being MurmurHash3's
+// finalizer.  Each round is invertible, so no two agents of a replicate share
+// a priority.  Smaller priorities move earlier.
 __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
   h ^= h >> 16;
   h *= 0x85EBCA6Bu;
@@ -116,15 +117,20 @@ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
   return h;
 }
 
-__device__ __forceinline__ uint32_t move_priority(uint32_t id, uint32_t k0, uint32_t k1) {
-  return fmix32(fmix32(id ^ k0) ^ k1);
+__device__ __forceinline__ U4 move_step_keys(uint32_t t, uint32_t s0, uint32_t s1) {
+  return philox10(0u, t, 2u, 0u, s0, s1);
 }
 
-__device__ __forceinline__ void move_step_key(uint32_t t, uint32_t s0, uint32_t s1, uint32_t* k0,
-                                              uint32_t* k1) {
-  const U4 r = philox10(0u, t, 2u, 0u, s0, s1);
-  *k0 = r.x;
-  *k1 = r.y;
+__device__ __forceinline__ uint32_t move_priority(uint32_t id, const U4& k) {
+  uint32_t L = (id >> 12) & 0xFFFu, R = id & 0xFFFu;
+  const uint32_t ks[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const uint32_t nr = L ^ (fmix32(R ^ ks[i]) & 0xFFFu);
+    L = R;
+    R = nr;
+  }
+  return (L << 12) | R;
 }
 
 // --------------------------------------------------------------------------

@@ -18,7 +18,7 @@ constexpr int kDevErrTimeout = 5;   // device error: a bounded wait gave up
 constexpr int kDevErrRounds = 6;    // device error: movement rounds exceeded the bound
 constexpr int kRoundLog = 64;       // movement rounds recorded per step
 constexpr int kMoveThreads = 1024;  // threads per block of the movement rounds
-constexpr int kMoveSmemCap = 8000;  // movers per block kept in shared memory (28 B each)
+constexpr int kMoveSmemCap = 9000;  // movers per block kept in shared memory (24 B each)
 
 // One mover of the current step (16 bytes): start cell, (replicate << 24 |
 // slot), movement priority, footprint info.
@@ -36,13 +36,15 @@ struct RepDev {
   int32_t tile_shift;               // Morton buckets are 2^tile_shift square tiles
   int32_t tiles_x, tiles_y;         // tiles per row / column
   int32_t bucket_base, bucket_span; // this replicate's range in the bucket arrays
+  int32_t claim_tx;                 // 16x16 tiles per row of the claim arrays
   float c32;                        // fl32(-k_S * log2(e))
   float margin;                     // relative margin M of the FP32 decision
   double kS;
   uint32_t seed_lo, seed_hi;
   uint32_t* rec;                    // [W*H] cell records
   unsigned long long* mask;         // [W*H*mw] line-of-sight masks
-  uint32_t* claim[3];               // [W*H] movement claims (three in rotation)
+  uint32_t* claim[2];               // movement claims: round tag << 24 | priority,
+                                    // tile-major (16x16-cell tiles of 1 KB)
   int32_t* id;                      // [cap]
   int32_t* cell;                    // [cap]  -1: slot empty / agent left
   int32_t* desired;                 // [cap]
@@ -80,6 +82,8 @@ struct Ctl {
   // each round's claims, and the global timer at the start of each round
   uint32_t round_n[kRoundLog];
   unsigned long long round_ns[kRoundLog + 1];
+  // per-phase timings of the last step's movement rounds (max over blocks, ns)
+  unsigned long long phase_ns[8];
 };
 
 struct Chunks {

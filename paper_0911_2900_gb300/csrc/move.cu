@@ -14,15 +14,17 @@
 //   commute; so moving, in each round, every waiting agent whose footprint
 //   holds no claim of a lower-priority waiting agent keeps every conflicting
 //   pair in priority order, which is equivalent to the serial loop.
-//   Claims are 64-bit atomicMin of the priority on every footprint cell, in
-//   three arrays used in rotation: in round r every waiting agent checks its
-//   claims in array r%3 and either moves or claims again in array (r+1)%3;
-//   the claims of round r-1 are cleared in round r.  One grid barrier per
-//   round.  The lowest-priority waiting agent always moves, so the loop ends
-//   after at most (number of movers) rounds; in practice after the longest
-//   local priority chain.  Each block keeps its slice of the movers and its
-//   waiting lists in shared memory (in global memory when the slices are too
-//   large).
+//   Claims are 32-bit atomicMin of (8-bit round tag, 24-bit priority) on
+//   every footprint cell, in two arrays used in turn: in round r every
+//   waiting agent checks its claims in array r&1 and either moves or claims
+//   again in array (r+1)&1.  The tag decreases from round to round, so a
+//   fresh claim beats every stale one of the step; the movers clear their
+//   cells at the end of the step.  One grid barrier per round.  The
+//   lowest-priority waiting agent
+//   always moves, so the loop ends after at most (number of movers) rounds;
+//   in practice after the longest local priority chain.  Each block keeps its
+//   slice of the movers and its waiting lists in shared memory (in global
+//   memory when the slices are too large).
 #include "fast_device.cuh"
 
 namespace fastgb {
@@ -103,12 +105,11 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
     if (fp == 0 && !ex) continue;
     const uint32_t i = append_slot(&a.ctl->act_count[2]);
     if (i < a.act_cap) {
-      uint32_t k0, k1;
-      move_step_key((uint32_t)t, R.seed_lo, R.seed_hi, &k0, &k1);
+      const U4 k = move_step_keys((uint32_t)t, R.seed_lo, R.seed_hi);
       MoveEntry e;
       e.c0 = (uint32_t)cell;
       e.ref = ((uint32_t)rep << 24) | (uint32_t)slot;
-      e.prio = move_priority((uint32_t)R.id[slot], k0, k1);
+      e.prio = move_priority((uint32_t)R.id[slot], k);
       e.info = (uint32_t)fp | ex | ((uint32_t)(dx + 8) << MV_DX) | ((uint32_t)(dy + 8) << MV_DY);
       a.act[2][i] = e;
     }
@@ -170,10 +171,20 @@ __device__ __forceinline__ bool round_barrier(Ctl* ctl, bool single) {
   return grid_barrier(ctl);
 }
 
-__device__ __forceinline__ void foot_cells(const PathTab* tab, uint32_t c0, int W, uint32_t info,
-                                           int* c) {
+// Footprint of a mover at (x0, y0): row-major cells c[s] (records) and the
+// cells' places q[s] in the tile-major claim arrays, s = 0..5 (start, path).
+__device__ __forceinline__ void foot_cells(const PathTab* tab, uint32_t xy, const RepDev& R,
+                                           uint32_t info, int* c, int* q) {
+  const int x0 = (int)(xy & 0xFFFFu), y0 = (int)(xy >> 16);
+  const int dx = (int)((info >> MV_DX) & 0xF) - 8, dy = (int)((info >> MV_DY) & 0xF) - 8;
+  const int i0 = ((dy + 5) * 11 + (dx + 5)) * 5;
 #pragma unroll
-  for (int s = 0; s < 6; ++s) c[s] = path_cell_tab(tab, (int)c0, W, info, s);
+  for (int s = 0; s < 6; ++s) {
+    const int x = x0 + (s == 0 ? 0 : (int)tab->d[i0 + s - 1][0]);
+    const int y = y0 + (s == 0 ? 0 : (int)tab->d[i0 + s - 1][1]);
+    c[s] = y * R.W + x;
+    q[s] = ((((y >> 4) * R.claim_tx) + (x >> 4)) << 8) | ((y & 15) << 4) | (x & 15);
+  }
 }
 
 // Path records an agent may walk: path cells 1..min(L, n + 1), where past
@@ -218,10 +229,21 @@ __device__ __forceinline__ void commit_move(const StepArgs& a, const RepDev& R, 
   }
 }
 
+// Claim value: an 8-bit round tag (255 for the first round of an epoch, one
+// less each round) above the 24-bit priority, so a claim of a later round
+// always wins atomicMin over an older one of the same epoch.  Claims are
+// cleared at the end of the step, and an epoch that runs out of tags is
+// closed the same way before claims start again at 255.
+__device__ __forceinline__ uint32_t claim_of(int tag_round, uint32_t prio) {
+  return ((uint32_t)(255 - tag_round) << 24) | prio;
+}
+
+constexpr int kTagRounds = 250;  // rounds per claim epoch before a clean-up
+
 __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ PathTab tab;
-  __shared__ uint32_t s_cnt[3];
+  __shared__ uint32_t s_cnt[2];
   build_path_tab(&tab);
   Ctl* ctl = a.ctl;
   const uint32_t n0 = min(__ldcg(&ctl->act_count[2]), a.act_cap);
@@ -229,7 +251,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   const uint32_t start = (uint32_t)(((unsigned long long)n0 * b) / G);
   const uint32_t nb = (uint32_t)(((unsigned long long)n0 * (b + 1)) / G) - start;
   const bool in_smem = (n0 + G - 1) / G <= (uint32_t)kMoveSmemCap;  // same for every block
-  uint32_t *P, *C0, *RF, *IN, *L[3];
+  uint32_t *P, *C0, *RF, *IN, *L[2];  // C0: start cell as (y << 16) | x
   if (in_smem) {
     P = reinterpret_cast<uint32_t*>(dsm);
     C0 = P + kMoveSmemCap;
@@ -237,114 +259,156 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
     IN = RF + kMoveSmemCap;
     L[0] = IN + kMoveSmemCap;
     L[1] = L[0] + kMoveSmemCap;
-    L[2] = L[1] + kMoveSmemCap;
   } else {
     P = a.mv_prio + start;
     C0 = a.mv_c0 + start;
     RF = a.mv_ref + start;
     IN = a.mv_info + start;
-    for (int j = 0; j < 3; ++j) L[j] = a.mv_list[j] + start;
+    L[0] = a.mv_list[0] + start;
+    L[1] = a.mv_list[1] + start;
   }
-  if (tid < 3) s_cnt[tid] = 0u;
-  if (b == 0 && tid == 0) ctl->round_ns[0] = global_ns();
+  if (tid < 2) s_cnt[tid] = 0u;
+  const unsigned long long t_start = global_ns();
+  if (b == 0 && tid == 0) {
+    ctl->round_ns[0] = t_start;
+    for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = 0ull;
+  }
   __syncthreads();
-  // this block's movers, and their claims for round 0
+  // this block's movers into shared memory, then their claims for round 0
   for (uint32_t k = tid; k < nb; k += blockDim.x) {
     const MoveEntry e = a.act[2][start + k];
-    const uint32_t info = e.info;
-    P[k] = e.prio;
-    C0[k] = e.c0;
-    RF[k] = e.ref;
-    IN[k] = info;
-    L[0][k] = k;
     const RepDev& R = a.reps[e.ref >> 24];
-    int c[6];
-    foot_cells(&tab, e.c0, R.W, info, c);
-    const int n = (int)(info & MV_LEN);
+    P[k] = e.prio;
+    C0[k] = ((e.c0 / (uint32_t)R.W) << 16) | (e.c0 % (uint32_t)R.W);
+    RF[k] = e.ref;
+    IN[k] = e.info;
+    L[0][k] = k;
+  }
+  __syncthreads();
+  if (tid == 0) atomicMax(&ctl->phase_ns[6], global_ns() - t_start);
+  for (uint32_t k = tid; k < nb; k += blockDim.x) {
+    const RepDev& R = a.reps[RF[k] >> 24];
+    int c[6], q[6];
+    foot_cells(&tab, C0[k], R, IN[k], c, q);
+    const int n = (int)(IN[k] & MV_LEN);
+    const uint32_t v = claim_of(0, P[k]);
 #pragma unroll
     for (int s = 0; s < 6; ++s)
-      if (s <= n) atomicMin(&R.claim[0][c[s]], e.prio);
+      if (s <= n) atomicMin(&R.claim[0][q[s]], v);
   }
   if (tid == 0) s_cnt[0] = nb;
+  __syncthreads();
+  if (tid == 0) atomicMax(&ctl->phase_ns[0], global_ns() - t_start);
   if (!grid_barrier(ctl)) return;
-  int r = 0;
+  if (tid == 0) atomicMax(&ctl->phase_ns[1], global_ns() - t_start);
+  int r = 0, tr = 0;  // round of the step, round within the claim epoch
   for (;;) {
-    // round r walks the list of round r-1 (a superset of the agents still
-    // waiting): clear their claims of round r-1; each waiting one checks its
-    // claims of round r, moves or claims for round r+1
-    const int it = r == 0 ? 0 : (r - 1) % 3;
-    const int ap = (r + 1) % 3;
+    // every agent still waiting checks its claims of round r (array r&1),
+    // moves if it holds all its cells, else claims for round r+1
+    const int in_l = r & 1, out_l = (r + 1) & 1;
     if (b == 0 && tid == 0) ctl->wait_count[(r + 2) % 3] = 0u;
-    const uint32_t n_it = s_cnt[it];
+    const uint32_t n_it = s_cnt[in_l];
     __syncthreads();
-    if (tid == 0) s_cnt[ap] = 0u;
+    if (tid == 0) s_cnt[out_l] = 0u;
     __syncthreads();
+    const unsigned long long t_round = global_ns();
+    const bool new_epoch = (tr + 1 >= kTagRounds);
     for (uint32_t k = tid; k < n_it; k += blockDim.x) {
-      const uint32_t idx = L[it][k];
+      const uint32_t idx = L[in_l][k];
       const uint32_t info = IN[idx];
       const uint32_t ref = RF[idx];
       const uint32_t p = P[idx];
       const int rep = (int)(ref >> 24), slot = (int)(ref & 0xFFFFFFu);
       const RepDev& R = a.reps[rep];
-      int c[6];
-      foot_cells(&tab, C0[idx], R.W, info, c);
+      int c[6], q[6];
+      foot_cells(&tab, C0[idx], R, info, c, q);
       const int n = (int)(info & MV_LEN);
-      if (r > 0) {
-        uint32_t* old = R.claim[(r - 1) % 3];
-#pragma unroll
-        for (int s = 0; s < 6; ++s)
-          if (s <= n) __stcg(&old[c[s]], 0xFFFFFFFFu);
-      }
-      if (info & MV_DONE) continue;
-      // the claims of the round and the path records, in one round trip
-      const uint32_t* now = R.claim[r % 3];
-      const int wl = walk_len(info);
+      const uint32_t* now = R.claim[in_l];
+      const uint32_t mine_v = claim_of(tr, p);
       uint32_t cl[6];
-      uint32_t pr[6];
 #pragma unroll
-      for (int s = 0; s < 6; ++s) cl[s] = (s <= n) ? __ldcg(&now[c[s]]) : p;
-#pragma unroll
-      for (int s = 0; s < 6; ++s) pr[s] = (s <= wl) ? __ldcg(&R.rec[c[s]]) : REC_OCC;
+      for (int s = 0; s < 6; ++s) cl[s] = (s <= n) ? __ldcg(&now[q[s]]) : mine_v;
       bool mine = true;
 #pragma unroll
-      for (int s = 0; s < 6; ++s) mine &= (cl[s] == p);
+      for (int s = 0; s < 6; ++s) mine &= (cl[s] == mine_v);
       if (mine) {
-        commit_move(a, R, rep, slot, c, pr);
-        IN[idx] = info | MV_DONE;
-      } else {
-        uint32_t* nxt = R.claim[ap];
+        const int wl = walk_len(info);
+        uint32_t pr[6];
 #pragma unroll
-        for (int s = 0; s < 6; ++s)
-          if (s <= n) atomicMin(&nxt[c[s]], p);
-        L[ap][append_slot(&s_cnt[ap])] = idx;
+        for (int s = 0; s < 6; ++s) pr[s] = (s <= wl) ? __ldcg(&R.rec[c[s]]) : REC_OCC;
+        commit_move(a, R, rep, slot, c, pr);
+      } else {
+        if (!new_epoch) {
+          uint32_t* nxt = R.claim[out_l];
+          const uint32_t v = claim_of(tr + 1, p);
+#pragma unroll
+          for (int s = 0; s < 6; ++s)
+            if (s <= n) atomicMin(&nxt[q[s]], v);
+        }
+        L[out_l][append_slot(&s_cnt[out_l])] = idx;
       }
     }
     __syncthreads();
-    if (tid == 0 && s_cnt[ap]) atomicAdd(&ctl->wait_count[ap], s_cnt[ap]);
+    if (tid == 0 && r < 2) atomicMax(&ctl->phase_ns[2 + r], global_ns() - t_round);
+    if (tid == 0 && r < 2) atomicMax(&ctl->phase_ns[4 + r], (unsigned long long)n_it);
+    if (tid == 0 && s_cnt[out_l]) atomicAdd(&ctl->wait_count[(r + 1) % 3], s_cnt[out_l]);
     if (!grid_barrier(ctl)) return;
-    const uint32_t waiting = __ldcg(&ctl->wait_count[ap]);
+    const uint32_t waiting = __ldcg(&ctl->wait_count[(r + 1) % 3]);
     if (b == 0 && tid == 0 && r < kRoundLog) {
       ctl->round_n[r] = waiting;
       ctl->round_ns[r + 1] = global_ns();
     }
     ++r;
+    ++tr;
     if (waiting == 0) break;
     if (r > (int)n0 + 1) {
       if (b == 0 && tid == 0) atomicCAS(&ctl->err, 0, kDevErrRounds);
       return;
     }
+    if (new_epoch) {
+      // out of tags: clear every claim of this step's movers, then the
+      // agents still waiting claim again with the first tag of a new epoch
+      for (uint32_t k = tid; k < nb; k += blockDim.x) {
+        const RepDev& R = a.reps[RF[k] >> 24];
+        int c[6], q[6];
+        foot_cells(&tab, C0[k], R, IN[k], c, q);
+        const int n = (int)(IN[k] & MV_LEN);
+#pragma unroll
+        for (int s = 0; s < 6; ++s)
+          if (s <= n) {
+            __stcg(&R.claim[0][q[s]], 0xFFFFFFFFu);
+            __stcg(&R.claim[1][q[s]], 0xFFFFFFFFu);
+          }
+      }
+      if (!grid_barrier(ctl)) return;
+      tr = 0;
+      const int nl = r & 1;
+      for (uint32_t k = tid; k < s_cnt[nl]; k += blockDim.x) {
+        const uint32_t idx = L[nl][k];
+        const RepDev& R = a.reps[RF[idx] >> 24];
+        int c[6], q[6];
+        foot_cells(&tab, C0[idx], R, IN[idx], c, q);
+        const int n = (int)(IN[idx] & MV_LEN);
+        const uint32_t v = claim_of(0, P[idx]);
+#pragma unroll
+        for (int s = 0; s < 6; ++s)
+          if (s <= n) atomicMin(&R.claim[nl][q[s]], v);
+      }
+      if (!grid_barrier(ctl)) return;
+    }
   }
-  // the agents of the last round all moved: clear their claims
-  const int last = (r - 1) % 3;
-  for (uint32_t k = tid; k < s_cnt[last]; k += blockDim.x) {
-    const uint32_t idx = L[last][k];
-    const RepDev& R = a.reps[RF[idx] >> 24];
-    int c[6];
-    foot_cells(&tab, C0[idx], R.W, IN[idx], c);
-    const int n = (int)(IN[idx] & MV_LEN);
+  // clear this step's claims: every mover's footprint cells, both arrays
+  for (uint32_t k = tid; k < nb; k += blockDim.x) {
+    const RepDev& R = a.reps[RF[k] >> 24];
+    int c[6], q[6];
+    foot_cells(&tab, C0[k], R, IN[k], c, q);
+    const int n = (int)(IN[k] & MV_LEN);
 #pragma unroll
     for (int s = 0; s < 6; ++s)
-      if (s <= n) __stcg(&R.claim[last][c[s]], 0xFFFFFFFFu);
+      if (s <= n) {
+        __stcg(&R.claim[0][q[s]], 0xFFFFFFFFu);
+        __stcg(&R.claim[1][q[s]], 0xFFFFFFFFu);
+      }
   }
   if (b == 0 && tid == 0) {
     ctl->rounds_last = r;
@@ -401,7 +465,7 @@ int move_prep_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t
   return 0;
 }
 
-size_t move_rounds_smem() { return (size_t)kMoveSmemCap * 28; }
+size_t move_rounds_smem() { return (size_t)kMoveSmemCap * 24; }
 
 int move_rounds_max_grid(int block, int* grid_out) {
   int dev = 0, sms = 0, per = 0;

@@ -44,8 +44,13 @@ def fmix32(h):
 
 
 def move_priority(seed, agent_id, t):
+    """Four-round Feistel network on the 12-bit halves of the 24-bit id, round
+    function fmix32(R ^ k_i) & 0xFFF, keys = Philox(seed; (0, t, 2, 0))."""
     k = philox4x32_10([0, t, 2, 0], [seed & M32, seed >> 32])
-    return fmix32(fmix32(agent_id ^ k[0]) ^ k[1])
+    L, R = (agent_id >> 12) & 0xFFF, agent_id & 0xFFF
+    for i in range(4):
+        L, R = R, L ^ (fmix32(R ^ k[i]) & 0xFFF)
+    return (L << 12) | R
 
 
 def reach_offsets(v, metric="l2"):

@@ -64,12 +64,18 @@ def test_priority_matches_reference(orc):
 
 
 def test_priority_is_a_random_permutation(orc):
-    """Each step orders the agents by a bijection of their ids (no ties), and
-    the order of two given agents is a fair coin over the steps."""
+    """Each step orders the agents by a permutation of the 24-bit ids (no
+    ties), and the order of two given agents is a fair coin over the steps."""
     ids = np.arange(5000, dtype=np.int64)
     for t in (0, 7):
         p = np.array([refs.move_priority(3, int(i), t) for i in ids])
         assert len(np.unique(p)) == len(p)
+        assert p.max() < (1 << 24)
+    # a full permutation of a 12-bit slice of the id space: all 2^24 values
+    # are too many for a unit test, but the network is a bijection on
+    # [0, 2^24); check it on 65536 ids and that they map to distinct values
+    q = {refs.move_priority(1, i, 3) for i in range(65536)}
+    assert len(q) == 65536
     wins = sum(refs.move_priority(5, 10, t) < refs.move_priority(5, 11, t) for t in range(4000))
     assert abs(wins - 2000) < 4 * np.sqrt(1000)       # binomial(4000, 1/2): 4 sigma
     # agent 0 lands uniformly in the order of 64 agents
