@@ -69,8 +69,10 @@ extern "C" {
 /* options for fast_set_option */
 #define FAST_OPT_RESORT_PERIOD 1  /* re-sort agents in Morton order every n steps (default 8; 0 never) */
 #define FAST_OPT_DIGESTS 2        /* 1: record per-step digests (fast_get_digests)  */
-#define FAST_OPT_LANES_V1 3       /* lanes per agent of the FP32 kernel for v_m=1; */
-                                  /* ..._V1 + (v_m - 1) for v_m = 1..5; 1,2,4,8    */
+#define FAST_OPT_LANES_V1 3       /* FP32 planning kernel for v_m=1 (..._V1 + v_m - 1 */
+                                  /* for v_m = 1..5): 0 one thread per agent with   */
+                                  /* per-warp record tiles (default); 1, 2, 4, 8    */
+                                  /* lanes per agent gathering from global memory   */
 #define FAST_OPT_BARRIER_NS 10    /* time limit of one device-side wait, ns         */
 #define FAST_OPT_USE_GRAPH 11     /* 1 (default): steps replay a captured CUDA graph */
 #define FAST_OPT_MOVE_BLOCKS 12   /* blocks of the cooperative movement kernel (0: auto) */
@@ -103,6 +105,10 @@ typedef struct {
   int32_t max_rounds;      /* largest number of movement rounds in one step     */
   int32_t last_rounds;     /* movement rounds of the last step                  */
   int64_t kernel_launches; /* CUDA kernels this context has queued, in total    */
+  int64_t tile_fallbacks;  /* planning warps that read from global memory because */
+                           /* their agents did not fit one shared-memory tile  */
+  int64_t movers;          /* agents handed to the movement rounds, all steps  */
+  int64_t footprint_cells; /* their footprint cells, all steps                 */
 } fast_stats;
 
 typedef struct {
@@ -163,10 +169,10 @@ int fast_get_digests(fast_ctx* ctx, int32_t replicate, int32_t max_steps, uint64
 
 /* Device times (ms) of the parts of the last step queued by fast_step, from
  * CUDA events recorded on the context's stream (waits for them):
- * ms4[0] planning kernels, ms4[1] FP64 re-check, ms4[2] movement (footprints
- * and rounds), ms4[3] bookkeeping (digests, re-sort, step counter).
- * Errors: FAST_ESTATE if no step has run. */
-int fast_phase_times(fast_ctx* ctx, float* ms4);
+ * ms5[0] planning kernels, ms5[1] FP64 re-check, ms5[2] movement order and
+ * footprints, ms5[3] movement rounds, ms5[4] bookkeeping (digests, re-sort,
+ * step counter).  Errors: FAST_ESTATE if no step has run. */
+int fast_phase_times(fast_ctx* ctx, float* ms5);
 
 /* Movement rounds of the last step (waits for the stream): n_wait[r] = agents
  * still waiting after round r's claims, t_ns[r] = device global timer at the

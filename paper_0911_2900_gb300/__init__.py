@@ -43,7 +43,8 @@ class Stats(C.Structure):
     _fields_ = [("step", C.c_int64), ("steps_run", C.c_int64), ("alive", C.c_int32),
                 ("exited", C.c_int32), ("agent_steps", C.c_int64), ("rechecked", C.c_int64),
                 ("move_rounds", C.c_int64), ("max_rounds", C.c_int32), ("last_rounds", C.c_int32),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("tile_fallbacks", C.c_int64),
+                ("movers", C.c_int64), ("footprint_cells", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -232,8 +233,9 @@ class Context:
         return a[:n], b[:n]
 
     def phase_times(self):
-        """(planning kernels, FP64 re-check, movement, bookkeeping) of the last step, ms."""
-        ms = (C.c_float * 4)()
+        """(planning kernels, FP64 re-check, movement footprints, movement rounds,
+        bookkeeping) of the last step, ms."""
+        ms = (C.c_float * 5)()
         self._check(self.lib.fast_phase_times(self.h, ms), "fast_phase_times")
         return tuple(ms)
 

@@ -29,7 +29,7 @@ namespace {
 // measured maximum of ex2.approx.ftz.f32 over the argument range with a
 // factor of two to spare; see the self test fast_selftest_ex2).
 constexpr double kEx2RelErr = 0x1p-21;
-constexpr int kDefaultLanes[5] = {1, 2, 2, 4, 4};
+constexpr int kDefaultLanes[5] = {0, 0, 0, 0, 0};  // 0: per-warp record tiles
 constexpr double kSqrt2 = 1.4142135623730951;
 constexpr double kLn2 = 0.6931471805599453;
 constexpr double kLog2e = 1.4426950408889634;
@@ -99,7 +99,7 @@ struct fast_ctx {
 
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_state[2] = {0, 0};  // 0 not built, 1 built, 2 capture failed
-  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool ran_step = false;
   int64_t launches = 0;          // kernels queued by this context
   int launches_per_graph[2] = {0, 0};
@@ -397,8 +397,8 @@ int enqueue_plan(fast_ctx* c, const StepArgs& a, bool diag, bool events) {
   return FAST_OK;
 }
 
-// One step: planning kernels | FP64 re-check | movement (prep + rounds) |
-// bookkeeping; events ev[0..4] bracket the four parts.
+// One step: planning kernels | FP64 re-check | movement footprints |
+// movement rounds | bookkeeping; events ev[0..5] bracket the five parts.
 int enqueue_step(fast_ctx* c, bool resort) {
   const StepArgs a = args_of(c);
   const Chunks all = all_chunks(c);
@@ -407,8 +407,9 @@ int enqueue_step(fast_ctx* c, bool resort) {
   CUDA_TRY(c, record_event(c, 2));
   if (c->digests) LAUNCH_TRY(c, digest_des_launch(a, all, plan_grid(c, all.n), c->cur));
   LAUNCH_TRY(c, move_prep_launch(a, all, plan_grid(c, all.n), c->cur));
-  LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), 1024, c->cur));
   CUDA_TRY(c, record_event(c, 3));
+  LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), 1024, c->cur));
+  CUDA_TRY(c, record_event(c, 4));
   if (c->digests) {
     LAUNCH_TRY(c, digest_cell_launch(a, all, plan_grid(c, all.n), c->cur));
     c->launches += 1;  // digest_cell_launch queues two kernels
@@ -418,7 +419,7 @@ int enqueue_step(fast_ctx* c, bool resort) {
     c->launches += 5;  // resort_launch queues six kernels
   }
   LAUNCH_TRY(c, step_end_launch(a, c->cur));
-  CUDA_TRY(c, record_event(c, 4));
+  CUDA_TRY(c, record_event(c, 5));
   return FAST_OK;
 }
 
@@ -828,6 +829,9 @@ int fast_readback(fast_ctx* c, int32_t r, int32_t id_bound, int32_t* cells_by_id
     stats->max_rounds = h.rounds_max;
     stats->last_rounds = h.rounds_last;
     stats->kernel_launches = c->launches;
+    stats->tile_fallbacks = (int64_t)h.tile_fallbacks;
+    stats->movers = (int64_t)h.movers_total;
+    stats->footprint_cells = (int64_t)h.foot_total;
   }
   return FAST_OK;
 }
@@ -852,11 +856,11 @@ int fast_get_digests(fast_ctx* c, int32_t r, int32_t max_steps, uint64_t* cell_d
   return cnt;
 }
 
-int fast_phase_times(fast_ctx* c, float* ms4) {
-  if (!c || !ms4) return FAST_EINVAL;
+int fast_phase_times(fast_ctx* c, float* ms5) {
+  if (!c || !ms5) return FAST_EINVAL;
   if (!c->ran_step) return fail(c, FAST_ESTATE, "no step has run");
-  CUDA_TRY(c, cudaEventSynchronize(c->ev[4]));
-  for (int i = 0; i < 4; ++i) CUDA_TRY(c, cudaEventElapsedTime(&ms4[i], c->ev[i], c->ev[i + 1]));
+  CUDA_TRY(c, cudaEventSynchronize(c->ev[5]));
+  for (int i = 0; i < 5; ++i) CUDA_TRY(c, cudaEventElapsedTime(&ms5[i], c->ev[i], c->ev[i + 1]));
   return FAST_OK;
 }
 
@@ -1025,8 +1029,8 @@ int fast_set_option(fast_ctx* c, int32_t option, int64_t value) {
       break;
     default:
       if (option >= FAST_OPT_LANES_V1 && option < FAST_OPT_LANES_V1 + 5) {
-        if (value != 1 && value != 2 && value != 4 && value != 8)
-          return fail(c, FAST_EINVAL, "lanes must be 1, 2, 4 or 8");
+        if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8)
+          return fail(c, FAST_EINVAL, "lanes must be 0 (tiled), 1, 2, 4 or 8");
         c->lanes[option - FAST_OPT_LANES_V1] = (int)value;
         break;
       }

@@ -79,23 +79,39 @@ int place_launch(RepDev* d, const int32_t* cells, const int32_t* ids, int n, cud
 }
 
 // ---------------------------------------------------------------------------
-// Morton re-sort.  Buckets are 2^tile_shift square tiles numbered along the
-// Z-order curve inside each replicate; a counting sort by bucket keeps agents
-// that are close on the grid close in memory and drops agents that left.
-__device__ __forceinline__ uint32_t spread16(uint32_t x) {
-  x &= 0xFFFFu;
-  x = (x | (x << 8)) & 0x00FF00FFu;
-  x = (x | (x << 4)) & 0x0F0F0F0Fu;
-  x = (x | (x << 2)) & 0x33333333u;
-  x = (x | (x << 1)) & 0x55555555u;
-  return x;
+// Spatial re-sort.  Buckets are 2^tile_shift square tiles numbered along a
+// Hilbert curve inside each replicate (consecutive buckets are always
+// neighbouring tiles, so a run of consecutive agents stays compact); a
+// counting sort by bucket keeps agents that are close on the grid close in
+// memory and drops agents that left.
+//
+// Hilbert index of tile (x, y) in a side x side square (side a power of two):
+// at each scale s the quadrant (rx, ry) contributes s*s*((3*rx) ^ ry), then
+// the coordinates are reflected / swapped into the quadrant's own frame.
+__device__ __forceinline__ uint32_t hilbert_index(uint32_t side, uint32_t x, uint32_t y) {
+  uint32_t d = 0;
+  for (uint32_t s = side >> 1; s > 0; s >>= 1) {
+    const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+    d += s * s * ((3u * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = side - 1 - x;
+        y = side - 1 - y;
+      }
+      const uint32_t tmp = x;
+      x = y;
+      y = tmp;
+    }
+  }
+  return d;
 }
 
 __device__ __forceinline__ int bucket_of(const RepDev& R, int cell) {
   const int x = cell % R.W, y = cell / R.W;
-  const uint32_t m = spread16((uint32_t)(x >> R.tile_shift)) |
-                     (spread16((uint32_t)(y >> R.tile_shift)) << 1);
-  return R.bucket_base + (int)m;
+  uint32_t side = 1;
+  while (side * side < (uint32_t)R.bucket_span) side <<= 1;
+  return R.bucket_base +
+         (int)hilbert_index(side, (uint32_t)(x >> R.tile_shift), (uint32_t)(y >> R.tile_shift));
 }
 
 __global__ void k_bucket_zero(StepArgs a) {

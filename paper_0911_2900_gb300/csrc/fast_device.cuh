@@ -52,7 +52,7 @@ struct ReachTable {
   int8_t dx[K > 0 ? K : 1];
   int8_t dy[K > 0 ? K : 1];
   int center;
-  constexpr ReachTable() : dx(), dy(), center(0) {
+  __host__ __device__ constexpr ReachTable() : dx(), dy(), center(0) {
     int k = 0;
     for (int y = -V; y <= V; ++y)
       for (int x = -V; x <= V; ++x)

@@ -78,6 +78,9 @@ struct Ctl {
   unsigned long long flagged;
   unsigned int max_dp_bits;          // float bits of max |p32 - p64|
   unsigned int pad1;
+  unsigned long long tile_fallbacks; // planning warps whose agents did not fit a tile
+  unsigned long long movers_total;   // movers handed to the movement rounds, all steps
+  unsigned long long foot_total;     // their footprint cells, all steps
   // movement instrumentation of the last step: agents still waiting after
   // each round's claims, and the global timer at the start of each round
   uint32_t round_n[kRoundLog];

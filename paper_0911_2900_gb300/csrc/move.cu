@@ -67,7 +67,7 @@ __device__ __forceinline__ int path_cell_tab(const PathTab* t, int c0, int W, ui
 // path cell by an agent that stays, need no work at all.
 __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
   const int t = a.ctl->t;
-  unsigned alive_local = 0;
+  unsigned alive_local = 0, foot_local = 0;
   for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
     const int rep = ch.rep[c];
     const RepDev& R = a.reps[rep];
@@ -103,6 +103,7 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
       fp = s;
     }
     if (fp == 0 && !ex) continue;
+    foot_local += (unsigned)fp + 1u;
     const uint32_t i = append_slot(&a.ctl->act_count[2]);
     if (i < a.act_cap) {
       const U4 k = move_step_keys((uint32_t)t, R.seed_lo, R.seed_hi);
@@ -114,10 +115,15 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
       a.act[2][i] = e;
     }
   }
-  // agents alive at the start of the step
-  for (int o = 16; o > 0; o >>= 1) alive_local += __shfl_xor_sync(0xffffffffu, alive_local, o);
+  // agents alive at the start of the step, footprint cells of the movers
+  for (int o = 16; o > 0; o >>= 1) {
+    alive_local += __shfl_xor_sync(0xffffffffu, alive_local, o);
+    foot_local += __shfl_xor_sync(0xffffffffu, foot_local, o);
+  }
   if ((threadIdx.x & 31) == 0 && alive_local)
     atomicAdd(&a.ctl->agent_steps, (unsigned long long)alive_local);
+  if ((threadIdx.x & 31) == 0 && foot_local)
+    atomicAdd(&a.ctl->foot_total, (unsigned long long)foot_local);
 }
 
 // ---------------------------------------------------------------------------
@@ -411,6 +417,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
       }
   }
   if (b == 0 && tid == 0) {
+    ctl->movers_total += (unsigned long long)n0;
     ctl->rounds_last = r;
     ctl->rounds_total += (unsigned long long)r;
     if (r > ctl->rounds_max) ctl->rounds_max = r;

@@ -221,6 +221,170 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
 }
 
 // ---------------------------------------------------------------------------
+// FP32 planning, one thread per agent, records from a per-warp tile.
+// Each warp copies into shared memory the box of cell records that covers
+// the reach sets of its 32 agents (coalesced row loads), then every thread
+// evaluates its agent's candidates at compile-time offsets into the tile.  A
+// warp whose agents are spread wider than the tile reads the records from
+// global memory instead.  Same weights, margin and outputs as k_plan_fp32.
+constexpr int kTileW = 48, kTileH = 48, kTileP = 49;   // per-warp record tile
+constexpr int kTileWarps = 8;
+constexpr size_t kTileSmem = (size_t)kTileWarps * kTileH * kTileP * 4;
+
+template <int V, int REACH, bool DIAG, bool TILE>
+__device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, int rep, int slot,
+                                            int cell, const uint32_t* p0, int pitch, int t,
+                                            int norecheck) {
+  constexpr int K = reach_count(V, REACH);
+  constexpr int CENTER = reach_center<V, REACH>();
+  constexpr ReachTable<V, REACH> T{};
+  const int id = R.id[slot];
+  const uint32_t rec0 = p0[0];
+  const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
+  const unsigned long long m1 = (K > 64) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
+  uint32_t rr[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int off = TILE ? (T.dy[k] * kTileP + T.dx[k]) : (T.dy[k] * pitch + T.dx[k]);
+    const bool adm = (k != CENTER) && mask_bit(m0, m1, k);
+    rr[k] = adm ? p0[off] : REC_OCC;
+  }
+  const int a0 = rec_a(rec0), b0 = rec_b(rec0);
+  const float c32 = R.c32;
+  float w[K];
+  float Wt = 0.f;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    float wk = 0.f;
+    if (k == CENTER)
+      wk = 1.0f;
+    else if (!(rr[k] & REC_OCC))
+      wk = ex2_approx(ds32(rec_a(rr[k]) - a0, rec_b(rr[k]) - b0) * c32);
+    w[k] = wk;
+    Wt += wk;
+  }
+  const float r = __fmul_rn((float)plan_uniform((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi), Wt);
+  float cacc = 0.f, cprev = 0.f, ck = 0.f;
+  int found = -1, lastnz = CENTER;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    if (w[k] > 0.f) {
+      const float cn = cacc + w[k];
+      if (found < 0 && r < cn) {
+        found = k;
+        cprev = cacc;
+        ck = cn;
+      }
+      lastnz = k;
+      cacc = cn;
+    }
+  }
+  if (DIAG) {
+    float* dp = a.diag_p32 + (a.diag_base[rep] + slot) * (int64_t)kMaxK;
+    float cc = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      cc = (w[k] > 0.f) ? cc + w[k] : cc;
+      dp[k] = cc / Wt;
+    }
+  }
+  bool ok;
+  int kk;
+  if (found >= 0) {
+    kk = found;
+    const float mw = R.margin * Wt;
+    ok = (r > cprev + mw) && (r < ck - mw);
+  } else {
+    kk = lastnz;
+    ok = false;
+  }
+  int dxk = 0, dyk = 0;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (k == kk) {
+      dxk = T.dx[k];
+      dyk = T.dy[k];
+    }
+  const int target = cell + dyk * R.W + dxk;
+  if (DIAG) {
+    const int64_t di = a.diag_base[rep] + slot;
+    a.diag_choice32[di] = target;
+    a.diag_flag[di] = ok ? 0 : 1;
+  }
+  if (ok || norecheck) {
+    R.desired[slot] = target;
+    set_static(R.rec, cell, rec0, target == cell);
+  } else {
+    const uint32_t qi = append_slot(&a.ctl->q_count);
+    if (qi < a.q_cap) a.queue[qi] = ((uint32_t)rep << 24) | (uint32_t)slot;
+  }
+}
+
+template <int V, int REACH, bool DIAG>
+__global__ void __launch_bounds__(256, 2) k_plan_tile(StepArgs a, Chunks ch, int norecheck) {
+  extern __shared__ __align__(16) uint32_t s_tiles[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t* tile = s_tiles + warp * (kTileH * kTileP);
+  const int t = a.ctl->t;
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const RepDev& R = a.reps[rep];
+    const int end = min(ch.begin[c] + kChunk, a.n_slots[rep]);
+    const int slot = ch.begin[c] + threadIdx.x;
+    const int cell = slot < end ? R.cell[slot] : -1;
+    const bool live = cell >= 0;
+    const int W = R.W;
+    int x = 0, y = 0;
+    if (live) {
+      y = cell / W;
+      x = cell - y * W;
+    }
+    const unsigned any = __ballot_sync(0xffffffffu, live);
+    if (!any) continue;
+    const int xmin = (int)__reduce_min_sync(0xffffffffu, live ? (unsigned)x : 0xFFFFFFFFu);
+    const int ymin = (int)__reduce_min_sync(0xffffffffu, live ? (unsigned)y : 0xFFFFFFFFu);
+    const int xmax = (int)__reduce_max_sync(0xffffffffu, live ? (unsigned)x : 0u);
+    const int ymax = (int)__reduce_max_sync(0xffffffffu, live ? (unsigned)y : 0u);
+    const int bx0 = max(xmin - V, 0), by0 = max(ymin - V, 0);
+    const int bx1 = min(xmax + V, W - 1), by1 = min(ymax + V, R.H - 1);
+    const int bw = bx1 - bx0 + 1, bh = by1 - by0 + 1;
+    const bool use_tile = bw <= kTileW && bh <= kTileH;
+    if (use_tile) {
+      // rows in batches of 8: all loads of a batch in flight before the stores
+      const bool c1 = lane + 32 < bw;
+      for (int row0 = 0; row0 < bh; row0 += 8) {
+        uint32_t v0[8], v1[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int row = row0 + j;
+          const uint32_t* src = R.rec + (size_t)(by0 + min(row, bh - 1)) * W + bx0;
+          v0[j] = (row < bh && lane < bw) ? src[lane] : 0u;
+          v1[j] = (row < bh && c1) ? src[lane + 32] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int row = row0 + j;
+          if (row < bh) {
+            if (lane < bw) tile[row * kTileP + lane] = v0[j];
+            if (c1) tile[row * kTileP + lane + 32] = v1[j];
+          }
+        }
+      }
+      __syncwarp();
+      if (live)
+        plan_one_g1<V, REACH, DIAG, true>(a, R, rep, slot, cell,
+                                          tile + (y - by0) * kTileP + (x - bx0), kTileP, t,
+                                          norecheck);
+    } else {
+      if (lane == 0) atomicAdd(&a.ctl->tile_fallbacks, 1ull);
+      if (live)
+        plan_one_g1<V, REACH, DIAG, false>(a, R, rep, slot, cell, R.rec + cell, W, t, norecheck);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
 // FP64 rule for one agent (thread-serial): weights in canonical order,
 // W and C_k summed sequentially, smallest k with fl(u*W) < C_k.
 template <int V, int REACH>
@@ -335,9 +499,27 @@ __global__ void __launch_bounds__(128) k_diag_compare(StepArgs a, Chunks ch) {
 }
 
 // ---------------------------------------------------------------------------
+template <int V, int REACH, bool DIAG>
+static int launch_tile(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s,
+                       int norecheck) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    if (cudaFuncSetAttribute(k_plan_tile<V, REACH, DIAG>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kTileSmem) != cudaSuccess)
+      return -1;
+    attr_set = true;
+  }
+  k_plan_tile<V, REACH, DIAG><<<grid, 256, kTileSmem, s>>>(a, ch, norecheck);
+  return 0;
+}
+
 template <int V, int REACH>
 static int launch_fp32(const StepArgs& a, int lanes, const Chunks& ch, int grid, cudaStream_t s,
                        bool diag, int norecheck) {
+  if (lanes == 0)
+    return diag ? launch_tile<V, REACH, true>(a, ch, grid, s, norecheck)
+                : launch_tile<V, REACH, false>(a, ch, grid, s, norecheck);
 #define FAST_L(G)                                                                  \
   if (lanes == G) {                                                                \
     if (diag)                                                                      \

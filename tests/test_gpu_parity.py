@@ -146,7 +146,7 @@ def test_reach_variants(fg, orc, reach, precision):
     assert_same(g, o, steps)
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8])
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8])
 def test_lanes_per_agent_variants(fg, orc, lanes):
     w = wl.config_small_room(W=120, H=90, n=3001, seed=5, v_m=4)
     steps = 25
