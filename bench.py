@@ -45,6 +45,42 @@ METRIC = "desired-cell choices/s and agent-steps/s at v_m=4, FP32+recheck vs FP6
 UNIT = "agent-steps/s"
 L2_FLUSH_BYTES = 512 << 20
 
+# Sources each profiled kernel is compiled from; a committed ncu summary's
+# DRAM traffic is reported only while these files are unchanged.
+KERNEL_SOURCES = {
+    "k_plan_tile": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
+    "k_move_rounds": ["move.cu", "fast_device.cuh", "fast_internal.h"],
+}
+
+
+def source_digest(kernel):
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_0911_2900_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, workload_name):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the
+    committed ncu summary of this kernel on this workload, or None when there
+    is none or the kernel's sources changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}.md")
+    try:
+        fields = {}
+        with open(path) as fh:
+            for ln in fh:
+                if ":" in ln and ln.split(":")[0] in ("source_digest", "dram_bytes_per_launch"):
+                    k, v = ln.split(":", 1)
+                    fields[k] = v.strip()
+        if fields.get("source_digest") != source_digest(kernel):
+            return None
+        return float(fields["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
 
 def parse():
     p = argparse.ArgumentParser()
@@ -398,14 +434,15 @@ def bench_ours(args):
                                                           for i, x in enumerate(ctx.last_move_phases)]},
             "roofline": {"bound": "hbm", "kernel": "k_move_rounds", "achieved": achieved_move,
                          "peak": peak, "unit": "GB/s", "frac": achieved_move / peak,
-                         "traffic": None, "peak_kind": peak_kind,
-                         "bytes_per_launch": bytes_move,
+                         "traffic": measured_traffic("k_move_rounds", w.name),
+                         "peak_kind": peak_kind, "bytes_per_launch": bytes_move,
                          "note": "dominant kernel; bound by the number of rounds and "
                                  "dependent scattered memory operations, not bandwidth"},
             "roofline_plan": {"bound": "hbm", "kernel": "k_plan_tile", "achieved": achieved,
                               "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                              "traffic": None, "peak_kind": peak_kind,
-                              "bytes_per_launch": bytes_plan, "union_cells": 0.5 * (u0 + u1)},
+                              "traffic": measured_traffic("k_plan_tile", w.name),
+                              "peak_kind": peak_kind, "bytes_per_launch": bytes_plan,
+                              "union_cells": 0.5 * (u0 + u1)},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * n_alive, "d2h_bytes_per_step": 8 * n0},
             "gpu_launches": int(launches),
