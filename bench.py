@@ -49,6 +49,7 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM traffic is reported only while these files are unchanged.
 KERNEL_SOURCES = {
     "k_plan_tile": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
+    "k_plan_fp32": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
     "k_move_rounds": ["move.cu", "fast_device.cuh", "fast_internal.h"],
 }
 
@@ -89,7 +90,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="precision",
-                   choices=["precision", "room", "corridors", "stress"])
+                   choices=["precision", "room", "corridors", "stress", "batch"])
+    p.add_argument("--no-tune", action="store_true")
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-steps", type=int, default=2)
@@ -105,16 +107,39 @@ def dist_env():
     return rank, world, local
 
 
-def make_workload(name, rank):
+def make_workloads(name, rank):
+    """The replicates one rank simulates (one context)."""
     from paper_0911_2900_gb300 import workloads as wl
 
     if name == "precision":
-        return wl.config_precision(seed=rank)
+        return [wl.config_precision(seed=rank)]
     if name == "room":
-        return wl.config_small_room(seed=rank)
+        return [wl.config_small_room(seed=rank)]
     if name == "corridors":
-        return wl.config_corridors(v_m=4, seed=rank)
-    return wl.config_stress(seed=rank)
+        return [wl.config_corridors(v_m=4, seed=rank)]
+    if name == "batch":
+        return wl.config_batch(seed=rank)
+    return [wl.config_stress(seed=rank)]
+
+
+def workload_label(works):
+    if len(works) == 1:
+        return works[0].name
+    n = sum(len(w.cells) for w in works)
+    return f"batch{len(works)}_{n // 1000}k_v1-5"
+
+
+def workload_config(works, name):
+    if len(works) == 1:
+        w = works[0]
+        return {"workload": w.name, "grid": f"{w.shape[1]}x{w.shape[0]}",
+                "agents": int(len(w.cells)), "v_m": w.v_m, "k_S": w.k_S, "reach": "l2"}
+    cells = sum(int(w.cell_type.size) for w in works)
+    return {"workload": workload_label(works), "replicates": len(works),
+            "grids": "log-uniform 100^2..2000^2 cells, aspect 1..2, 10% obstacles, 1-4 exits",
+            "cells_total": cells, "agents": int(sum(len(w.cells) for w in works)),
+            "v_m": {str(v): sum(w.v_m == v for w in works) for v in range(1, 6)},
+            "k_S": works[0].k_S, "reach": "l2"}
 
 
 def measured_peaks():
@@ -204,52 +229,67 @@ def move_bytes(movers, footprint_cells):
     return movers * (8 + 12) + footprint_cells * 4
 
 
-def cpu_oracle_rate(w, steps, threads):
+def oracle_sample(works, max_agents=1_200_000):
+    """Replicates the CPU oracle times: all of them, or for a batch every
+    k-th replicate so that about max_agents agents take part."""
+    total = sum(len(w.cells) for w in works)
+    if total <= max_agents or len(works) == 1:
+        return list(range(len(works)))
+    k = max(1, int(round(total / max_agents)))
+    return list(range(0, len(works), k))
+
+
+def cpu_oracle_rate(works, steps, threads, warmup=0):
+    """The FP64 CPU oracle as it stands: planning on `threads` threads with
+    the paper's OpenMP partition, movement serial, on the sampled replicates."""
     import oracle
 
-    sim = oracle.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed)
-    sim.place(w.cells)
-    r = sim.run(0, steps, threads=threads, digests=False)
-    agent_steps = int(len(w.cells)) + int(r["alive"][:-1].sum()) if steps > 1 else len(w.cells)
-    plan_s, move_s = r["plan_s"], r["move_s"]
+    agent_steps, plan_s, move_s = 0, 0.0, 0.0
+    idx = oracle_sample(works)
+    for i in idx:
+        w = works[i]
+        sim = oracle.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed)
+        sim.place(w.cells)
+        if warmup:
+            sim.run(0, warmup, threads=threads, digests=False)
+        alive0 = int((sim.cell >= 0).sum())
+        r = sim.run(warmup, steps, threads=threads, digests=False)
+        agent_steps += alive0 + (int(r["alive"][:-1].sum()) if steps > 1 else 0)
+        plan_s += r["plan_s"]
+        move_s += r["move_s"]
+    n = sum(len(works[i].cells) for i in idx)
+    sample = (f"{steps} steps of {len(idx)} of {len(works)} replicates ({n} agents)"
+              if len(works) > 1 else f"{steps} steps of {works[0].name} ({n} agents)")
+    if warmup:
+        sample += f" after {warmup} warm-up steps"
     return dict(agent_steps=agent_steps, plan_s=plan_s, move_s=move_s,
-                value=agent_steps / (plan_s + move_s),
-                choices_per_s=agent_steps / plan_s)
+                value=agent_steps / (plan_s + move_s), choices_per_s=agent_steps / plan_s,
+                sample=sample + f"; planning on {threads} threads (paper's OpenMP partition), "
+                                "movement serial")
 
 
 def bench_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    w = make_workload(args.workload, 0)
+    works = make_workloads(args.workload, 0)
     threads = os.cpu_count() or 1
-    import oracle
-
-    sim = oracle.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed)
-    sim.place(w.cells)
-    if args.warmup:
-        sim.run(0, args.warmup, threads=threads, digests=False)
-    alive0 = int((sim.cell >= 0).sum())
     t0 = time.perf_counter()
-    r = sim.run(args.warmup, args.steps, threads=threads, digests=False)
+    c = cpu_oracle_rate(works, args.steps, threads, warmup=args.warmup)
     wall = time.perf_counter() - t0
-    agent_steps = alive0 + int(r["alive"][:-1].sum())
-    value = agent_steps / (r["plan_s"] + r["move_s"])
+    cfg = workload_config(works, args.workload)
+    cfg["precision"] = "fp64 (CPU oracle)"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": c["value"], "unit": UNIT, "n_gpus": 0,
         "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * (r["plan_s"] + r["move_s"]) / args.steps,
+        "ms_per_step": 1e3 * (c["plan_s"] + c["move_s"]) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": w.name, "grid": f"{w.shape[1]}x{w.shape[0]}",
-                   "agents": int(len(w.cells)), "v_m": w.v_m, "k_S": w.k_S,
-                   "precision": "fp64 (CPU oracle)"},
-        "choices_per_s": agent_steps / r["plan_s"],
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{args.steps} full steps of {w.name} after {args.warmup} "
-                                   f"warm-up steps; planning on {threads} threads with the "
-                                   f"paper's OpenMP partition, movement serial"},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "data": "synthetic", "config": cfg,
+        "choices_per_s": c["choices_per_s"],
+        "cpu_baseline": {"value": c["value"], "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": c["sample"]},
+        "e2e": {"value": c["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
         "wall_s": wall,
     }
     print(json.dumps(line), flush=True)
@@ -277,12 +317,17 @@ def bench_ours(args):
 
             dist.barrier()
 
-    w = make_workload(args.workload, rank)
-    n0 = int(len(w.cells))
+    works = make_workloads(args.workload, rank)
+    label = workload_label(works)
+    n_rep = len(works)
+    n0 = [int(len(w.cells)) for w in works]
+    mask_words = [1 if w.v_m <= 4 else 2 for w in works]
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    loop_graph = args.workload == "batch"
 
     def timed_steps(ctx, k, record_phases=True):
+        """Per-step CUDA-event times, the L2 flushed before each step."""
         step_ms, phases = [], []
         for i in range(k):
             flush.fill_(i)
@@ -297,13 +342,44 @@ def bench_ours(args):
                 phases.append(ctx.phase_times())
         return step_ms, phases
 
+    def timed_loop(ctx, k):
+        """The k-step loop as one captured graph launch (inputs larger than
+        L2), captured before the timed launch; events around the launch."""
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(k)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    def union_bytes(ctx, alive):
+        return sum(plan_bytes(alive[r], ctx.reach_union(r), mask_words[r]) for r in range(n_rep))
+
+    def alive_now(ctx):
+        return [ctx.readback(r, 0)[2]["alive"] for r in range(n_rep)]
+
+    def make_ctx(precision):
+        ctx = fg.Context(n_rep, precision)
+        for r, w in enumerate(works):
+            ctx.init_grid(r, w.cell_type, w.k_S, w.v_m, w.seed)
+            ctx.place(r, w.cells)
+        return ctx
+
     # ---- FP32 + FP64 re-check -------------------------------------------------
-    ctx = fg.Context(1, "fp32_recheck")
-    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
-    ctx.place(0, w.cells)
-    ctx.step(args.warmup)
+    ctx = make_ctx("fp32_recheck")
+    tune = ctx.autotune(trials=3) if not args.no_tune else None
+    if loop_graph:
+        # warm-up steps, then capture the timed loop's graph with an untimed
+        # run of the same length at the same step phase (period 8)
+        ctx.step(args.warmup)
+        ctx.step(args.steps)
+        ctx.step((-args.steps) % 8)
+    else:
+        timed_steps(ctx, args.warmup, record_phases=False)
     torch.cuda.synchronize()
-    u0 = ctx.reach_union(0)
+    al0 = alive_now(ctx)
+    b0 = union_bytes(ctx, al0)
     _, _, st0 = ctx.readback(0, 0)
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
@@ -312,16 +388,34 @@ def bench_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     t_wall = time.perf_counter()
-    step_ms, phases = timed_steps(ctx, args.steps)
+    if loop_graph:
+        step_ms = [timed_loop(ctx, args.steps) / args.steps] * args.steps
+    else:
+        step_ms, phases = timed_steps(ctx, args.steps)
     torch.cuda.synchronize()
     barrier()
     t_wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     _, _, st1 = ctx.readback(0, 0)
     mv_wait, mv_us = ctx.move_profile()
-    u1 = ctx.reach_union(0)
+    al1 = alive_now(ctx)
+    b1 = union_bytes(ctx, al1)
     agent_steps = st1["agent_steps"] - st0["agent_steps"]
     launches = st1["kernel_launches"] - st0["kernel_launches"]
+    movers = (st1["movers"] - st0["movers"]) / args.steps
+    foot = (st1["footprint_cells"] - st0["footprint_cells"]) / args.steps
+    rounds_per_step = (st1["move_rounds"] - st0["move_rounds"]) / args.steps
+    rechecked = (st1["rechecked"] - st0["rechecked"]) / args.steps
+    fallbacks = (st1["tile_fallbacks"] - st0["tile_fallbacks"]) / args.steps
+    if loop_graph:
+        # phase breakdown, and the FP32 form timed like the FP64 form below
+        # (per step, L2 flushed), from a few extra steps not in the value
+        _, _, sp0 = ctx.readback(0, 0)
+        ms32, phases = timed_steps(ctx, max(args.fp64_steps, min(4, args.steps)))
+        _, _, sp1 = ctx.readback(0, 0)
+        step32_value = (sp1["agent_steps"] - sp0["agent_steps"]) / (sum(ms32) / 1e3)
+    else:
+        step32_value = None
     T = sum(step_ms) / 1e3
     plan_ms = [p[0] for p in phases]
     recheck_ms = [p[1] for p in phases]
@@ -331,23 +425,21 @@ def bench_ours(args):
     T_max = max_over_ranks(T, world)
     total_agent_steps = max_over_ranks(agent_steps, world, op="sum")
     value = total_agent_steps / T_max
-    choices = total_agent_steps / max_over_ranks((sum(plan_ms) + sum(recheck_ms)) / 1e3, world)
-    n_avg = agent_steps / args.steps
-    mw = 1 if w.v_m <= 4 else 2
-    bytes_plan = plan_bytes(n_avg, 0.5 * (u0 + u1), mw)
-    mean_plan_s = statistics.mean(plan_ms) / 1e3
+    plan_frac = (sum(plan_ms) + sum(recheck_ms)) / max(1e-9, sum(sum(p) for p in phases))
+    choices = total_agent_steps / max_over_ranks(T * plan_frac, world)
+    bytes_plan = 0.5 * (b0 + b1)
     peak, peak_kind = measured_peaks()
-    achieved = bytes_plan / mean_plan_s / 1e9
-    movers = (st1["movers"] - st0["movers"]) / args.steps
-    foot = (st1["footprint_cells"] - st0["footprint_cells"]) / args.steps
+    achieved = bytes_plan / (statistics.mean(plan_ms) / 1e3) / 1e9
     bytes_move = move_bytes(movers, foot)
-    mean_rounds_s = statistics.mean(rounds_ms) / 1e3
-    achieved_move = bytes_move / mean_rounds_s / 1e9
+    achieved_move = bytes_move / (statistics.mean(rounds_ms) / 1e3) / 1e9
+
+    # the planning kernel the tuned context runs for v_m = 4 (or its only v_m)
+    v_main = 4 if any(w.v_m == 4 for w in works) else works[0].v_m
+    lanes_main = tune["lanes"][v_main - 1] if tune is not None else 0
+    plan_kernel = "k_plan_tile" if lanes_main == 0 else "k_plan_fp32"
 
     # ---- the all-FP64 form ------------------------------------------------------
-    ctx64 = fg.Context(1, "fp64")
-    ctx64.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
-    ctx64.place(0, w.cells)
+    ctx64 = make_ctx("fp64")
     ctx64.step(1)
     torch.cuda.synchronize()
     _, _, s640 = ctx64.readback(0, 0)
@@ -360,32 +452,40 @@ def bench_ours(args):
     ctx64.close()
 
     # ---- end to end through the public API with host buffers ---------------------
-    cells_d, _, st = ctx.readback(0, n0)
-    alive_ids = np.flatnonzero(cells_d >= 0).astype(np.int32)
-    n_alive = len(alive_ids)
-    h_cells = torch.empty(n_alive, dtype=torch.int32, pin_memory=True).numpy()
-    h_ids = torch.empty(n_alive, dtype=torch.int32, pin_memory=True).numpy()
-    out_cells = torch.empty(n0, dtype=torch.int32, pin_memory=True).numpy()
-    out_des = torch.empty(n0, dtype=torch.int32, pin_memory=True).numpy()
-    h_cells[:] = cells_d[alive_ids]
-    h_ids[:] = alive_ids
-    t_step = st["step"]
+    hc, hi, oc, od = [], [], [], []
+    t_step = None
+    for r in range(n_rep):
+        cells_d, _, st = ctx.readback(r, n0[r])
+        t_step = st["step"]
+        ids = np.flatnonzero(cells_d >= 0).astype(np.int32)
+        a = torch.empty(len(ids), dtype=torch.int32, pin_memory=True).numpy()
+        b = torch.empty(len(ids), dtype=torch.int32, pin_memory=True).numpy()
+        a[:] = cells_d[ids]
+        b[:] = ids
+        hc.append(a)
+        hi.append(b)
+        oc.append(torch.empty(n0[r], dtype=torch.int32, pin_memory=True).numpy())
+        od.append(torch.empty(n0[r], dtype=torch.int32, pin_memory=True).numpy())
+    h2d = 8 * sum(len(a) for a in hc)
+    d2h = 8 * sum(n0)
     e2e_agent_steps = 0
     barrier()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter()
     for i in range(args.e2e_steps):
-        ctx.place(0, h_cells, ids=h_ids, start_step=t_step)
+        for r in range(n_rep):
+            ctx.place(r, hc[r], ids=hi[r], start_step=t_step)
         ctx.step(1)
-        ctx.readback(0, n0, cells_out=out_cells, desired_out=out_des)
-        e2e_agent_steps += len(h_cells)
-        keep = out_cells[h_ids] >= 0
-        h_ids_new = h_ids[keep]
-        h_cells_new = out_cells[h_ids_new]
-        h_cells = h_cells[:len(h_ids_new)]
-        h_ids = h_ids[:len(h_ids_new)]
-        h_cells[:] = h_cells_new
-        h_ids[:] = h_ids_new
+        for r in range(n_rep):
+            ctx.readback(r, n0[r], cells_out=oc[r], desired_out=od[r])
+            e2e_agent_steps += len(hc[r])
+            keep = oc[r][hi[r]] >= 0
+            ids_new = hi[r][keep]
+            cells_new = oc[r][ids_new]
+            hc[r] = hc[r][:len(ids_new)]
+            hi[r] = hi[r][:len(ids_new)]
+            hc[r][:] = cells_new
+            hi[r][:] = ids_new
         t_step += 1
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t_e2e
@@ -397,58 +497,67 @@ def bench_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
-        c = cpu_oracle_rate(w, args.cpu_steps, threads)
+        c = cpu_oracle_rate(works, args.cpu_steps, threads)
         cpu = {"value": c["value"], "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {args.cpu_steps} steps of {w.name} ({n0} agents); planning "
-                         f"on {threads} threads (paper's OpenMP partition), movement serial",
-               "choices_per_s": c["choices_per_s"]}
+               "sample": c["sample"], "choices_per_s": c["choices_per_s"]}
 
     if rank == 0:
+        cfg = workload_config(works, args.workload)
+        cfg.update({"precision": "fp32 weights + fp64 re-check",
+                    "l2": ("inputs larger than L2 (cell records alone "
+                           f"{4 * cfg.get('cells_total', 0) / 1e6:.0f} MB); the {args.steps}-step "
+                           "loop timed as one graph launch" if loop_graph else
+                           "flushed before every timed step (512 MiB write, outside events)"),
+                    "parallelism": f"replicas x{world}"})
+        if tune is not None:
+            cfg["autotuned"] = {"tile_shift": tune["tile_shift"],
+                                "lanes_by_v": {str(v + 1): l for v, l in enumerate(tune["lanes"])
+                                               if l >= 0}}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * T_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": w.name, "grid": f"{w.shape[1]}x{w.shape[0]}",
-                       "agents": n0, "v_m": w.v_m, "k_S": w.k_S, "reach": "l2",
-                       "precision": "fp32 weights + fp64 re-check",
-                       "l2": "flushed before every timed step (512 MiB write, outside events)",
-                       "parallelism": f"replicas x{world}"},
+            "config": cfg,
             "choices_per_s": choices,
             "fp64_form": {"value": fp64_value, "choices_per_s": fp64_choices, "unit": UNIT,
-                          "steps": args.fp64_steps},
-            "speedup_vs_fp64_form": value / fp64_value,
+                          "steps": args.fp64_steps,
+                          "timing": "per step, L2 flushed before each"},
             "phase_ms": {"plan": statistics.mean(plan_ms), "recheck": statistics.mean(recheck_ms),
                          "move_prep": statistics.mean(prep_ms),
                          "move_rounds": statistics.mean(rounds_ms),
                          "other": statistics.mean(other_ms)},
             "movers_per_step": movers,
-            "rechecked_per_step": (st1["rechecked"] - st0["rechecked"]) / args.steps,
-            "tile_fallback_warps_per_step": (st1["tile_fallbacks"] - st0["tile_fallbacks"]) / args.steps,
-            "move_rounds_per_step": (st1["move_rounds"] - st0["move_rounds"]) / args.steps,
+            "rechecked_per_step": rechecked,
+            "tile_fallback_warps_per_step": fallbacks,
+            "move_rounds_per_step": rounds_per_step,
             "move_last_step": {"waiting_after_round": [int(x) for x in mv_wait[:12]],
                                "round_us": [round(float(x), 2) for x in mv_us[:12]],
                                "rounds": int(len(mv_wait)),
-                               "phases_max_over_blocks": [round(float(x) / 1e3, 2) if i not in (4, 5) else int(x)
+                               "phases_max_over_blocks": [round(float(x) / 1e3, 2) if i not in (4, 5, 6) else int(x)
                                                           for i, x in enumerate(ctx.last_move_phases)]},
             "roofline": {"bound": "hbm", "kernel": "k_move_rounds", "achieved": achieved_move,
                          "peak": peak, "unit": "GB/s", "frac": achieved_move / peak,
-                         "traffic": measured_traffic("k_move_rounds", w.name),
+                         "traffic": measured_traffic("k_move_rounds", label),
                          "peak_kind": peak_kind, "bytes_per_launch": bytes_move,
                          "note": "dominant kernel; bound by the number of rounds and "
                                  "dependent scattered memory operations, not bandwidth"},
-            "roofline_plan": {"bound": "hbm", "kernel": "k_plan_tile", "achieved": achieved,
+            "roofline_plan": {"bound": "hbm", "kernel": plan_kernel, "achieved": achieved,
                               "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                              "traffic": measured_traffic("k_plan_tile", w.name),
-                              "peak_kind": peak_kind, "bytes_per_launch": bytes_plan,
-                              "union_cells": 0.5 * (u0 + u1)},
+                              "traffic": measured_traffic(plan_kernel, label),
+                              "peak_kind": peak_kind, "bytes_per_launch": bytes_plan},
             "e2e": {"value": e2e_value, "unit": UNIT,
-                    "h2d_bytes_per_step": 8 * n_alive, "d2h_bytes_per_step": 8 * n0},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "clocks": clk,
             "wall_s_timed": t_wall,
         }
+        if step32_value is None:
+            line["speedup_vs_fp64_form"] = value / fp64_value
+        else:
+            line["fp32_form_per_step_timing"] = step32_value
+            line["speedup_vs_fp64_form"] = step32_value / fp64_value
         if cpu is not None:
             line["cpu_baseline"] = cpu
         s = json.dumps(line)

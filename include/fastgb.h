@@ -77,6 +77,17 @@ extern "C" {
 #define FAST_OPT_USE_GRAPH 11     /* 1 (default): steps replay a captured CUDA graph */
 #define FAST_OPT_MOVE_BLOCKS 12   /* blocks of the cooperative movement kernel (0: auto) */
 #define FAST_OPT_TILE_SHIFT 13    /* Morton bucket side = 2^shift cells (default 4) */
+#define FAST_OPT_GRAPH_STEPS 14   /* fast_step(n) with 2 <= n <= this (default 512)  */
+                                  /* runs the whole n-step loop as one captured     */
+                                  /* CUDA graph, kept for later calls at the same   */
+                                  /* step phase; 0 or 1: one graph per step         */
+#define FAST_OPT_CLAIM_RESERVE 15 /* movement claim tags (255 per clean-up of the   */
+                                  /* claim arrays) a step must have left, else the  */
+                                  /* arrays are cleared first (default 96; a step   */
+                                  /* that runs out clears them itself)              */
+#define FAST_OPT_CLAIM_TAG 16     /* clears the claims and sets the next step's     */
+                                  /* first claim tag, 0..254: a test hook for the   */
+                                  /* clean-ups; results do not depend on it         */
 
 typedef struct fast_ctx fast_ctx;
 
@@ -87,7 +98,7 @@ typedef void (*fast_free_fn)(void* ptr, void* user);
 
 /* One replicate's grid. */
 typedef struct {
-  int32_t width, height;    /* cells; width*height < 2^31                   */
+  int32_t width, height;    /* cells, each <= 65535; width*height < 2^31     */
   const uint8_t* cell_type; /* host [width*height], borrowed for the call    */
   double k_S;               /* coupling to the static floor field (>= 0)     */
   int32_t v_m;              /* maximum speed, 1..5 cells per step            */
@@ -119,6 +130,17 @@ typedef struct {
   double max_abs_dp;       /* max |P32(k) - P64(k)| over cumulative probabilities */
   double margin;           /* relative margin M of the FP32 decision           */
 } fast_precision_report;
+
+typedef struct {
+  int32_t tile_shift;      /* chosen re-sort bucket side, log2 of cells          */
+  int32_t lanes[5];        /* chosen planning variant per v_m (FAST_OPT_LANES_V1 */
+                           /* values: 0 tiled, 1/2/4/8 lanes per agent); -1 for  */
+                           /* a v_m no replicate uses                           */
+  float shift_us[4];       /* planning (tiled) + re-sort / period, us per step,  */
+                           /* for bucket shifts 3, 4, 5, 6                       */
+  float lanes_us[5][5];    /* [v_m - 1][variant]: planning time of that v_m's    */
+                           /* agents, us, variants 0, 1, 2, 4, 8; 0: not tried  */
+} fast_tune_report;
 
 /* Creates a context for n_replicates independent replicates (1..256).
  * precision: FAST_FP64 / FAST_FP32_RECHECK / FAST_FP32_NORECHECK;
@@ -175,13 +197,14 @@ int fast_get_digests(fast_ctx* ctx, int32_t replicate, int32_t max_steps, uint64
 int fast_phase_times(fast_ctx* ctx, float* ms5);
 
 /* Movement rounds of the last step (waits for the stream): n_wait[r] = agents
- * still waiting after round r's claims, t_ns[r] = device global timer at the
- * start of round r (t_ns has one entry more).  Writes min(max_rounds, 64)
- * rounds; returns the number of rounds of the step or a negative error.
- * With max_rounds >= 73, t_ns[65..72] also receive per-phase maxima over the
- * blocks (ns; load of the movers and first claims, the same plus the grid
- * barrier, the work of rounds 0 and 1, and the movers per block in rounds 0
- * and 1 as counts). */
+ * still waiting after round r, t_ns[r] = device global timer at the start of
+ * round r (t_ns has one entry more).  Writes min(max_rounds, 64) rounds;
+ * returns the number of rounds of the step or a negative error.  With
+ * max_rounds >= 73, t_ns[65..72] also receive maxima over the blocks: the
+ * first round's work (ns), the same plus its grid barrier (ns), the second
+ * round's work (ns), the first round's claims (ns), movers per block, movers
+ * per block still waiting after the first round, the round from which one
+ * block finished alone (0: none), 0. */
 int fast_move_profile(fast_ctx* ctx, int32_t max_rounds, uint32_t* n_wait, uint64_t* t_ns);
 
 /* Runs the FP32 planning of the current state without re-check next to the
@@ -212,6 +235,20 @@ int fast_reach_union(fast_ctx* ctx, int32_t replicate, int64_t* cells);
  * fast_plan_only since its last fast_init_grid / fast_place_agents. */
 int fast_plan_noalloc(fast_ctx* ctx, int32_t replicate, int32_t step, int32_t id_bound,
                       int32_t* desired_by_id_dev);
+
+/* Autotuner (the paper has no counterpart: it chooses how the GPU runs the
+ * planning phase, never what it computes).  On the agents placed now, times
+ * `trials` planning passes (after one untimed pass) of each candidate:
+ * first the re-sort bucket side 2^3..2^6 cells with the tiled kernel (plus
+ * the re-sort's own time divided by its period), then, at the chosen side,
+ * each planning variant for every v_m present.  The fastest choices become
+ * the context's options (FAST_OPT_TILE_SHIFT, FAST_OPT_LANES_V*); agents are
+ * re-sorted, which permutes storage only.  The step index and every agent's
+ * cell are unchanged; the desired cells of the last step are overwritten (a
+ * step re-plans them anyway).  `out` (may be NULL) receives the choices and
+ * the times.  With precision FAST_FP64 nothing is tuned.  Errors:
+ * FAST_EINVAL (trials not in 1..1000), FAST_ESTATE (no agents), FAST_ECUDA. */
+int fast_autotune(fast_ctx* ctx, int32_t trials, fast_tune_report* out);
 
 int fast_set_option(fast_ctx* ctx, int32_t option, int64_t value);
 const char* fast_last_error(const fast_ctx* ctx);

@@ -23,7 +23,7 @@ PRECISION = {"fp64": 0, "fp32_recheck": 1, "fp32_norecheck": 2}
 REACH = {"l2": 0, "l2p": 1, "linf": 2}
 OPT = {"resort_period": 1, "digests": 2, "lanes_v1": 3, "lanes_v2": 4, "lanes_v3": 5,
        "lanes_v4": 6, "lanes_v5": 7, "barrier_ns": 10, "use_graph": 11, "move_blocks": 12,
-       "tile_shift": 13}
+       "tile_shift": 13, "graph_steps": 14, "claim_reserve": 15, "claim_tag": 16}
 ERRORS = {0: "FAST_OK", -1: "FAST_EINVAL", -2: "FAST_ESTATE", -3: "FAST_ENOMEM",
           -4: "FAST_ECUDA", -5: "FAST_ETIMEOUT"}
 
@@ -58,6 +58,19 @@ class PrecisionReport(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class TuneReport(C.Structure):
+    _fields_ = [("tile_shift", C.c_int32), ("lanes", C.c_int32 * 5), ("shift_us", C.c_float * 4),
+                ("lanes_us", (C.c_float * 5) * 5)]
+
+    def as_dict(self):
+        return {"tile_shift": self.tile_shift, "lanes": list(self.lanes),
+                "shift_us": {3 + i: float(self.shift_us[i]) for i in range(4)},
+                "lanes_us": {v + 1: {l: float(self.lanes_us[v][j])
+                                     for j, l in enumerate((0, 1, 2, 4, 8))
+                                     if self.lanes_us[v][j] > 0}
+                             for v in range(5) if self.lanes[v] >= 0}}
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 
@@ -81,6 +94,7 @@ EXPORTS = {
     "fast_reach_union": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fast_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "fast_plan_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+    "fast_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fast_last_error": (C.c_char_p, [C.c_void_p]),
     "fast_destroy": (None, [C.c_void_p]),
     "fast_selftest_exp64": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
@@ -266,6 +280,46 @@ class Context:
         self._check(self.lib.fast_plan_noalloc(self.h, rep, int(step), int(out_by_id.numel()),
                                                C.c_void_p(out_by_id.data_ptr())),
                     "fast_plan_noalloc")
+
+    def autotune(self, trials: int = 5, cache: str | None = None, key: str | None = None):
+        """Runs the library's autotuner (fast_autotune) and returns its report
+        as a dict.  With `cache` (a JSON file path) and `key` (a caller's
+        description of the workload), a choice stored under that key and this
+        GPU's name is applied instead of tuning again, and a new one is
+        stored."""
+        import json
+
+        full_key = None
+        if cache is not None and key is not None:
+            import torch
+
+            full_key = f"{torch.cuda.get_device_name(self.device)}|{key}"
+            try:
+                with open(cache) as f:
+                    stored = json.load(f).get(full_key)
+            except (OSError, ValueError):
+                stored = None
+            if stored is not None:
+                self.set_option("tile_shift", stored["tile_shift"])
+                for v, l in enumerate(stored["lanes"]):
+                    if l >= 0:
+                        self.set_option(f"lanes_v{v + 1}", l)
+                return dict(stored, cached=True)
+        rep = TuneReport()
+        self._check(self.lib.fast_autotune(self.h, int(trials), C.byref(rep)), "fast_autotune")
+        out = rep.as_dict()
+        if full_key is not None:
+            try:
+                with open(cache) as f:
+                    table = json.load(f)
+            except (OSError, ValueError):
+                table = {}
+            table[full_key] = out
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, default=str)
+            os.replace(tmp, cache)
+        return dict(out, cached=False)
 
     def set_option(self, name: str, value: int):
         self._check(self.lib.fast_set_option(self.h, OPT[name], int(value)), "fast_set_option")

@@ -6,10 +6,12 @@
 // move.cu and aux.cu; the host only computes the exact floor field at grid
 // set-up (floor_field.cpp) and checks placements.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -71,7 +73,6 @@ struct fast_ctx {
   int32_t* d_exited = nullptr;
   uint32_t* d_queue = nullptr;
   MoveEntry* d_act[3] = {nullptr, nullptr, nullptr};
-  uint32_t* d_act_info[3] = {nullptr, nullptr, nullptr};
   uint32_t* d_mv_prio = nullptr;
   uint32_t* d_mv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 
@@ -99,6 +100,13 @@ struct fast_ctx {
 
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int graph_state[2] = {0, 0};  // 0 not built, 1 built, 2 capture failed
+  // step loops captured whole, keyed by (step index mod re-sort period, steps);
+  // a null executable records a capture that failed
+  struct Multi {
+    cudaGraphExec_t exec = nullptr;
+    int launches = 0;
+  };
+  std::map<std::pair<int, int>, Multi> multi;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   bool ran_step = false;
   int64_t launches = 0;          // kernels queued by this context
@@ -112,6 +120,8 @@ struct fast_ctx {
   bool use_graph = true;
   int move_blocks = 0;
   int tile_shift = 4;
+  int graph_steps = 512;  // longest step loop captured as one graph
+  bool resort_pending = false;  // agents placed since the last spatial sort
 
   int64_t t_host = 0;
   int64_t steps_since_place = 0;
@@ -236,6 +246,9 @@ void drop_graphs(fast_ctx* c) {
     c->graph[i] = nullptr;
     c->graph_state[i] = 0;
   }
+  for (auto& kv : c->multi)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  c->multi.clear();
 }
 
 // Work chunks (replicate, first slot) per v_m group and over all replicates;
@@ -309,13 +322,13 @@ int rebuild_layout(fast_ctx* c) {
   if (total_cap > c->list_cap) {
     dfree(c, c->d_queue);
     dfree(c, c->d_act[2]);
-    dfree(c, c->d_act_info[2]);
+    dfree(c, c->d_act[0]);
     dfree(c, c->d_mv_prio);
     for (auto& p : c->d_mv) dfree(c, p);
     const size_t n = (size_t)total_cap;
     if (int e = alloc_into(c, &c->d_queue, n)) return e;
     if (int e = alloc_into(c, &c->d_act[2], n)) return e;
-    if (int e = alloc_into(c, &c->d_act_info[2], n)) return e;
+    if (int e = alloc_into(c, &c->d_act[0], n)) return e;
     if (int e = alloc_into(c, &c->d_mv_prio, n)) return e;
     for (auto& p : c->d_mv)
       if (int e = alloc_into(c, &p, n)) return e;
@@ -345,7 +358,6 @@ StepArgs args_of(fast_ctx* c) {
   a.q_cap = c->list_cap;
   for (int i = 0; i < 3; ++i) {
     a.act[i] = c->d_act[i];
-    a.act_info[i] = c->d_act_info[i];
     a.mv_list[i] = c->d_mv[3 + i];
   }
   a.mv_prio = c->d_mv_prio;
@@ -407,6 +419,7 @@ int enqueue_step(fast_ctx* c, bool resort) {
   CUDA_TRY(c, record_event(c, 2));
   if (c->digests) LAUNCH_TRY(c, digest_des_launch(a, all, plan_grid(c, all.n), c->cur));
   LAUNCH_TRY(c, move_prep_launch(a, all, plan_grid(c, all.n), c->cur));
+  c->launches += 2;  // move_prep_launch queues three kernels
   CUDA_TRY(c, record_event(c, 3));
   LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), 1024, c->cur));
   CUDA_TRY(c, record_event(c, 4));
@@ -461,6 +474,44 @@ int build_graph(fast_ctx* c, int which) {
   return FAST_OK;
 }
 
+// Captures the next n steps (re-sorts where the step index calls for one) as
+// one graph; on any capture failure the entry stays null and steps are
+// queued one graph at a time instead.
+int build_multi(fast_ctx* c, int n, fast_ctx::Multi* out) {
+  out->exec = nullptr;
+  out->launches = 0;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return FAST_OK;
+  }
+  c->cur = c->cap_stream;
+  const int64_t before = c->launches;
+  const std::string err_before = c->err;
+  int e = FAST_OK;
+  for (int i = 0; i < n && e == FAST_OK; ++i) {
+    const int64_t t = c->t_host + i;
+    e = enqueue_step(c, c->resort_period > 0 && ((t + 1) % c->resort_period == 0));
+  }
+  c->cur = c->stream;
+  out->launches = (int)(c->launches - before);
+  c->launches = before;
+  cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+  if (e != FAST_OK || ce != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    c->poisoned = false;
+    c->err = err_before;
+    return FAST_OK;
+  }
+  if (cudaGraphInstantiate(&out->exec, g, 0) != cudaSuccess) {
+    cudaGetLastError();
+    out->exec = nullptr;
+  }
+  cudaGraphDestroy(g);
+  return FAST_OK;
+}
+
 int write_ctl_int(fast_ctx* c, size_t offset, int32_t v) {
   CUDA_TRY(c, cudaMemcpyAsync((char*)c->d_ctl + offset, &v, 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -482,6 +533,18 @@ int check_device_error(fast_ctx* c) {
 
 // ===========================================================================
 extern "C" {
+
+// Queues the spatial sort that placements leave pending (one for any number
+// of fast_place_agents calls in a row).
+int sort_if_pending(fast_ctx* c) {
+  if (!c->resort_pending) return FAST_OK;
+  const StepArgs a = args_of(c);
+  const Chunks all = all_chunks(c);
+  LAUNCH_TRY(c, resort_launch(a, all, plan_grid(c, all.n), true, c->stream));
+  c->launches += 5;
+  c->resort_pending = false;
+  return FAST_OK;
+}
 
 static int create_impl(fast_ctx* c, int32_t n_replicates);
 
@@ -533,6 +596,7 @@ static int create_impl(fast_ctx* c, int32_t n_replicates) {
   Ctl h{};
   h.resort_period = c->resort_period;
   h.barrier_ns_limit = (unsigned long long)c->barrier_ns;
+  h.tag_reserve = 96;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_ctl, &h, sizeof h, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_nslots, 0, 4 * n_replicates, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(c->d_exited, 0, 4 * n_replicates, c->stream));
@@ -544,7 +608,8 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   if (!c) return FAST_EINVAL;
   if (c->poisoned) return FAST_ESTATE;
   if (!rep_ok(c, r) || !g) return fail(c, FAST_EINVAL, "bad replicate index or NULL grid");
-  if (g->width < 1 || g->height < 1 || (int64_t)g->width * g->height >= ((int64_t)1 << 31))
+  if (g->width < 1 || g->height < 1 || g->width > 65535 || g->height > 65535 ||
+      (int64_t)g->width * g->height >= ((int64_t)1 << 31))
     return fail(c, FAST_EINVAL, "grid %d x %d out of range", g->width, g->height);
   if (!g->cell_type) return fail(c, FAST_EINVAL, "cell_type is NULL");
   if (g->v_m < 1 || g->v_m > 5) return fail(c, FAST_EINVAL, "v_m = %d not in 1..5", g->v_m);
@@ -713,9 +778,8 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
   CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->dig_count, &zero, 4, cudaMemcpyHostToDevice, c->stream));
   const StepArgs a = args_of(c);
   LAUNCH_TRY(c, step_begin_launch(a, c->stream));
-  // initial Morton order
-  const Chunks all = all_chunks(c);
-  LAUNCH_TRY(c, resort_launch(a, all, plan_grid(c, all.n), true, c->stream));
+  // the spatial order of the new agents is made once, before the next step
+  c->resort_pending = true;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->t_host = start_step;
   c->steps_since_place = 0;
@@ -731,6 +795,7 @@ int fast_step(fast_ctx* c, int32_t n_steps) {
   if (!any) return fail(c, FAST_ESTATE, "no agents placed");
   if (c->layout_dirty)
     if (int e = rebuild_layout(c)) return e;
+  if (int e = sort_if_pending(c)) return e;
   if (c->digests && c->steps_since_place + n_steps > c->dig_cap) {
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     const int32_t want = (int32_t)std::max<int64_t>(1024, 2 * (c->steps_since_place + n_steps));
@@ -752,6 +817,30 @@ int fast_step(fast_ctx* c, int32_t n_steps) {
     c->d_dig_des = dd;
     c->dig_cap = want;
     drop_graphs(c);
+  }
+  if (c->use_graph && n_steps >= 2 && n_steps <= c->graph_steps) {
+    const int phase = c->resort_period > 0 ? (int)(c->t_host % c->resort_period) : 0;
+    const auto key = std::make_pair(phase, (int)n_steps);
+    auto it = c->multi.find(key);
+    if (it == c->multi.end()) {
+      if (c->multi.size() >= 8) {
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        for (auto& kv : c->multi)
+          if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        c->multi.clear();
+      }
+      fast_ctx::Multi m;
+      if (int e = build_multi(c, n_steps, &m)) return e;
+      it = c->multi.emplace(key, m).first;
+    }
+    if (it->second.exec) {
+      CUDA_TRY(c, cudaGraphLaunch(it->second.exec, c->stream));
+      c->launches += it->second.launches;
+      c->t_host += n_steps;
+      c->steps_since_place += n_steps;
+      c->ran_step = true;
+      return FAST_OK;
+    }
   }
   for (int32_t i = 0; i < n_steps; ++i) {
     const bool resort = c->resort_period > 0 && ((c->t_host + 1) % c->resort_period == 0);
@@ -780,11 +869,152 @@ int fast_plan_only(fast_ctx* c, int32_t n) {
   if (!any) return fail(c, FAST_ESTATE, "no agents placed");
   if (c->layout_dirty)
     if (int e = rebuild_layout(c)) return e;
+  if (int e = sort_if_pending(c)) return e;
   const StepArgs a = args_of(c);
   for (int32_t i = 0; i < n; ++i) {
     LAUNCH_TRY(c, step_begin_launch(a, c->stream));
     if (int e = enqueue_plan(c, a, false, false)) return e;
   }
+  return FAST_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: times the planning kernels on the context's own agents and keeps
+// the fastest re-sort bucket size and, per v_m group, the fastest planning
+// variant.  Choices change speed only: every variant computes the same
+// desired cells.
+namespace {
+
+constexpr int kTuneShifts[4] = {3, 4, 5, 6};
+constexpr int kTuneLanes[5] = {0, 1, 2, 4, 8};
+
+// Mean time (us) of `trials` planning passes of group gi (-1: every group)
+// with the context's current variants; one untimed pass first.
+int time_planning(fast_ctx* c, int gi, int trials, cudaEvent_t e0, cudaEvent_t e1, float* us) {
+  const StepArgs a = args_of(c);
+  for (int i = 0; i <= trials; ++i) {
+    if (i == 1) CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+    LAUNCH_TRY(c, step_begin_launch(a, c->stream));
+    for (int g = 0; g < (int)c->groups.size(); ++g) {
+      if (gi >= 0 && g != gi) continue;
+      const auto& G = c->groups[g];
+      Chunks ch{G.d_rep, G.d_begin, G.n};
+      LAUNCH_TRY(c, plan_groups_launch(a, G.v, c->reach, c->lanes[G.v - 1], c->precision, ch,
+                                       plan_grid(c, G.n), c->stream, false));
+    }
+  }
+  CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+  CUDA_TRY(c, cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+  *us = 1e3f * ms / (float)trials;
+  return FAST_OK;
+}
+
+int time_resort(fast_ctx* c, int trials, cudaEvent_t e0, cudaEvent_t e1, float* us) {
+  const StepArgs a = args_of(c);
+  const Chunks all = all_chunks(c);
+  for (int i = 0; i <= trials; ++i) {
+    if (i == 1) CUDA_TRY(c, cudaEventRecord(e0, c->stream));
+    LAUNCH_TRY(c, resort_launch(a, all, plan_grid(c, all.n), true, c->stream));
+  }
+  CUDA_TRY(c, cudaEventRecord(e1, c->stream));
+  CUDA_TRY(c, cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CUDA_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+  *us = 1e3f * ms / (float)trials;
+  return FAST_OK;
+}
+
+int apply_shift(fast_ctx* c, int shift) {
+  c->tile_shift = shift;
+  c->layout_dirty = true;
+  if (int e = rebuild_layout(c)) return e;
+  const StepArgs a = args_of(c);
+  const Chunks all = all_chunks(c);
+  LAUNCH_TRY(c, resort_launch(a, all, plan_grid(c, all.n), true, c->stream));
+  c->launches += 5;
+  c->resort_pending = false;
+  return FAST_OK;
+}
+
+int autotune_impl(fast_ctx* c, int trials, fast_tune_report* rep, cudaEvent_t e0,
+                  cudaEvent_t e1) {
+  // 1. bucket size: planning with the tiled kernel everywhere, plus the
+  //    re-sort amortised over its period
+  int saved[5];
+  std::memcpy(saved, c->lanes, sizeof saved);
+  for (int v = 0; v < 5; ++v) c->lanes[v] = 0;
+  int best_shift = c->tile_shift;
+  float best = 1e30f;
+  for (int i = 0; i < 4; ++i) {
+    if (int e = apply_shift(c, kTuneShifts[i])) return e;
+    float plan_us = 0.f, sort_us = 0.f;
+    if (int e = time_planning(c, -1, trials, e0, e1, &plan_us)) return e;
+    if (int e = time_resort(c, 1, e0, e1, &sort_us)) return e;
+    const float per_step = plan_us + (c->resort_period > 0 ? sort_us / c->resort_period : 0.f);
+    rep->shift_us[i] = per_step;
+    if (per_step < best) {
+      best = per_step;
+      best_shift = kTuneShifts[i];
+    }
+  }
+  if (int e = apply_shift(c, best_shift)) return e;
+  rep->tile_shift = best_shift;
+  // 2. planning variant per v_m group
+  for (int v = 0; v < 5; ++v) rep->lanes[v] = -1;
+  for (int g = 0; g < (int)c->groups.size(); ++g) {
+    const int v = c->groups[g].v;
+    int best_l = 0;
+    float best_t = 1e30f;
+    for (int j = 0; j < 5; ++j) {
+      c->lanes[v - 1] = kTuneLanes[j];
+      float us = 0.f;
+      if (int e = time_planning(c, g, trials, e0, e1, &us)) return e;
+      rep->lanes_us[v - 1][j] = us;
+      if (us < best_t) {
+        best_t = us;
+        best_l = kTuneLanes[j];
+      }
+    }
+    c->lanes[v - 1] = best_l;
+    rep->lanes[v - 1] = best_l;
+  }
+  for (int v = 0; v < 5; ++v)
+    if (rep->lanes[v] < 0) c->lanes[v] = saved[v];
+  return FAST_OK;
+}
+
+}  // namespace
+
+int fast_autotune(fast_ctx* c, int32_t trials, fast_tune_report* out) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (trials < 1 || trials > 1000) return fail(c, FAST_EINVAL, "trials not in 1..1000");
+  bool any = false;
+  for (auto& R : c->reps) any = any || R.placed;
+  if (!any) return fail(c, FAST_ESTATE, "no agents placed");
+  fast_tune_report rep{};
+  rep.tile_shift = c->tile_shift;
+  for (int v = 0; v < 5; ++v) rep.lanes[v] = -1;
+  if (c->precision != FAST_FP64) {
+    if (c->layout_dirty)
+      if (int e = rebuild_layout(c)) return e;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      return fail(c, FAST_ECUDA, "cudaEventCreate failed");
+    }
+    const int e = autotune_impl(c, trials, &rep, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e) return e;
+    if (int e2 = check_device_error(c)) return e2;
+    drop_graphs(c);
+  }
+  if (out) *out = rep;
   return FAST_OK;
 }
 
@@ -890,6 +1120,7 @@ int fast_precision_report_run(fast_ctx* c, fast_precision_report* out) {
   if (!any) return fail(c, FAST_ESTATE, "no agents placed");
   if (c->layout_dirty)
     if (int e = rebuild_layout(c)) return e;
+  if (int e = sort_if_pending(c)) return e;
   std::vector<int64_t> base(c->n_rep, 0);
   int64_t total = 0;
   double margin = 0.0;
@@ -1026,6 +1257,24 @@ int fast_set_option(fast_ctx* c, int32_t option, int64_t value) {
       if (value < 0 || value > 10) return fail(c, FAST_EINVAL, "tile shift not in 0..10");
       c->tile_shift = (int)value;
       c->layout_dirty = true;
+      break;
+    case FAST_OPT_CLAIM_RESERVE:
+      if (value < 0 || value > 254) return fail(c, FAST_EINVAL, "claim reserve not in 0..254");
+      if (int e = write_ctl_int(c, offsetof(Ctl, tag_reserve), (int32_t)value)) return e;
+      break;
+    case FAST_OPT_CLAIM_TAG:
+      // any tag is safe once no claim is left
+      if (value < 0 || value > 254) return fail(c, FAST_EINVAL, "claim tag not in 0..254");
+      for (auto& R : c->reps) {
+        if (!R.grid_set) continue;
+        const size_t n = (size_t)((R.W + 15) / 16) * ((R.H + 15) / 16) * 256;
+        for (auto p : R.d.claim) CUDA_TRY(c, cudaMemsetAsync(p, 0xFF, n * 4, c->stream));
+      }
+      if (int e = write_ctl_int(c, offsetof(Ctl, claim_tag), (int32_t)value)) return e;
+      break;
+    case FAST_OPT_GRAPH_STEPS:
+      if (value < 0 || value > 4096) return fail(c, FAST_EINVAL, "graph steps not in 0..4096");
+      c->graph_steps = (int)value;
       break;
     default:
       if (option >= FAST_OPT_LANES_V1 && option < FAST_OPT_LANES_V1 + 5) {

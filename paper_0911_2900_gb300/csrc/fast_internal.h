@@ -68,7 +68,9 @@ struct Ctl {
   int32_t resort_period;      // re-sort agents every this many steps (0: never)
   int32_t digests_on;
   int32_t dig_count;          // digests written
-  int32_t pad0;
+  uint32_t tail_count;        // waiting movers handed to one block, this step
+  uint32_t claim_tag;         // tag of the next step's first movement claims
+  uint32_t tag_reserve;       // clear the claims before a step with fewer tags left
   unsigned long long rounds_total;
   unsigned long long rechecked_total;
   unsigned long long agent_steps;
@@ -103,8 +105,7 @@ struct StepArgs {
   int32_t* exited;       // [n_rep] agents that left through an exit, total
   uint32_t* queue;       // [q_cap] FP64 re-check queue (rep << 24 | slot)
   uint32_t q_cap;
-  MoveEntry* act[3];     // [2]: movers of the step
-  uint32_t* act_info[3]; // [2]: per mover footprint length, exit flag, (dx, dy)
+  MoveEntry* act[3];     // [2]: movers of the step; [0]: movers one block finishes
   uint32_t act_cap;
   // movement state when a block's movers do not fit its shared memory
   uint32_t *mv_prio, *mv_c0, *mv_ref, *mv_info, *mv_list[3];

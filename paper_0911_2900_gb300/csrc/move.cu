@@ -15,16 +15,19 @@
 //   holds no claim of a lower-priority waiting agent keeps every conflicting
 //   pair in priority order, which is equivalent to the serial loop.
 //   Claims are 32-bit atomicMin of (8-bit round tag, 24-bit priority) on
-//   every footprint cell, in two arrays used in turn: in round r every
-//   waiting agent checks its claims in array r&1 and either moves or claims
-//   again in array (r+1)&1.  The tag decreases from round to round, so a
-//   fresh claim beats every stale one of the step; the movers clear their
-//   cells at the end of the step.  One grid barrier per round.  The
-//   lowest-priority waiting agent
-//   always moves, so the loop ends after at most (number of movers) rounds;
-//   in practice after the longest local priority chain.  Each block keeps its
-//   slice of the movers and its waiting lists in shared memory (in global
-//   memory when the slices are too large).
+//   every footprint cell, in two arrays used in turn.  The tag falls with a
+//   round counter that runs on across steps, so a fresh claim beats every
+//   stale one; the arrays are cleared only when the tags run out (every few
+//   steps).  In a round with tag g every waiting agent checks its claims in
+//   array g&1 and either moves or claims again, with tag g+1, in the other
+//   array.  One grid barrier per round.  The lowest-priority
+//   waiting agent always moves, so the loop ends after at most (number of
+//   movers) rounds; in practice after the longest local priority chain.
+//   An agent that moves in the first round moves exactly as the records read
+//   by the movement-order pass say (nobody touched its footprint before it),
+//   so it only flips occupancy bits.  Waiting agents are kept per block in
+//   shared memory when they fit; once few are left, one block takes them all
+//   and finishes the step with block-level barriers.
 #include "fast_device.cuh"
 
 namespace fastgb {
@@ -34,7 +37,52 @@ constexpr uint32_t MV_LEN = 0x7u;      // footprint path length (0..5)
 constexpr uint32_t MV_EXIT = 0x8u;     // the path reaches an exit cell after the footprint
 constexpr int MV_DX = 4;               // dx + 8, 4 bits
 constexpr int MV_DY = 8;               // dy + 8, 4 bits
-constexpr uint32_t MV_DONE = 0x1000u;  // moved
+constexpr int MV_FIN = 13;             // first-round outcome: last path step entered (3 bits)
+constexpr uint32_t MV_GONE = 1u << 16; // first-round outcome: leaves through an exit
+
+constexpr int kTail = 1024;            // waiting movers one block finishes alone
+
+// Claim value: an 8-bit round tag g (0..kTags-1; the value falls as g grows)
+// above the 24-bit priority, so a claim of a later round always wins
+// atomicMin over an older one.  Tags run on from step to step; the claim
+// arrays are cleared, and g restarts at 0, before a step that would start
+// with fewer than ctl->tag_reserve tags left, and within a step that runs out.
+constexpr uint32_t kTags = 255;
+__device__ __forceinline__ uint32_t claim_of(uint32_t g, uint32_t prio) {
+  return ((254u - g) << 24) | prio;
+}
+
+// Sets every claim of every replicate to "none": grid-stride, or by the
+// calling block alone.
+__device__ __forceinline__ void clear_all_claims(const StepArgs& a, bool block_only = false) {
+  const uint32_t stride = block_only ? blockDim.x : gridDim.x * blockDim.x;
+  const uint32_t first = block_only ? threadIdx.x : blockIdx.x * blockDim.x + threadIdx.x;
+  for (int r = 0; r < a.n_rep; ++r) {
+    const RepDev& R = a.reps[r];
+    if (!R.claim[0]) continue;
+    const uint32_t n = (uint32_t)R.claim_tx * (uint32_t)((R.H + 15) >> 4) * 256u;
+    for (uint32_t i = first; i < n; i += stride) {
+      __stcg(&R.claim[0][i], 0xFFFFFFFFu);
+      __stcg(&R.claim[1][i], 0xFFFFFFFFu);
+    }
+  }
+}
+
+// Before the movement-order pass: clear the claims if this step could run
+// out of tags.
+__global__ void __launch_bounds__(256) k_claim_epoch(StepArgs a) {
+  if (__ldcg(&a.ctl->claim_tag) + a.ctl->tag_reserve <= kTags) return;
+  clear_all_claims(a);
+}
+
+__global__ void k_claim_epoch_done(StepArgs a) {
+  if (threadIdx.x == 0 && a.ctl->claim_tag + a.ctl->tag_reserve > kTags) a.ctl->claim_tag = 0u;
+}
+
+// Place of cell (x, y) in the tile-major claim arrays (16x16-cell tiles).
+__device__ __forceinline__ int claim_index(const RepDev& R, int x, int y) {
+  return ((((y >> 4) * R.claim_tx) + (x >> 4)) << 8) | ((y & 15) << 4) | (x & 15);
+}
 
 // Straight-path table for every offset (dx, dy) in [-5, 5]^2 and step
 // s = 1..5: (dx_s, dy_s) = (q(s*dx, L), q(s*dy, L)), L = max(|dx|, |dy|),
@@ -63,8 +111,9 @@ __device__ __forceinline__ int path_cell_tab(const PathTab* t, int c0, int W, ui
 }
 
 // ---------------------------------------------------------------------------
-// Footprints of all movers; agents that stay, or are blocked at their first
-// path cell by an agent that stays, need no work at all.
+// Footprints, priorities and first-round outcomes of all movers; agents that
+// stay, or are blocked at their first path cell by an agent that stays, need
+// no work at all.
 __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
   const int t = a.ctl->t;
   unsigned alive_local = 0, foot_local = 0;
@@ -84,17 +133,17 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
     const int dx = des % W - x0, dy = des / W - y0;
     const int L = max(abs(dx), abs(dy));
     // all path records first (independent loads), then the scan
-    uint32_t pr[5];
+    uint32_t pr[6];
 #pragma unroll
     for (int s = 1; s <= 5; ++s)
-      pr[s - 1] = (s <= L) ? R.rec[(y0 + div_half_away(s * dy, L)) * W +
-                                   (x0 + div_half_away(s * dx, L))]
-                           : REC_STA;
+      pr[s] = (s <= L) ? R.rec[(y0 + div_half_away(s * dy, L)) * W +
+                               (x0 + div_half_away(s * dx, L))]
+                       : REC_STA;
     int fp = 0;
     uint32_t ex = 0;
 #pragma unroll
     for (int s = 1; s <= 5; ++s) {
-      const uint32_t r = pr[s - 1];
+      const uint32_t r = pr[s];
       if (s > L || (r & REC_STA)) break;
       if (rec_exit(r)) {
         ex = MV_EXIT;
@@ -103,15 +152,33 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
       fp = s;
     }
     if (fp == 0 && !ex) continue;
+    // the walk if nobody touches the footprint first: up to the first
+    // occupied cell, or into an exit
+    int fin = 0;
+    bool gone = false, stop = false;
+#pragma unroll
+    for (int s = 1; s <= 5; ++s) {
+      const uint32_t r = pr[s];
+      stop = stop || s > L || (r & REC_OCC);
+      if (!stop) {
+        fin = s;
+        if (rec_exit(r)) {
+          gone = true;
+          stop = true;
+        }
+      }
+    }
     foot_local += (unsigned)fp + 1u;
+    const U4 k = move_step_keys((uint32_t)t, R.seed_lo, R.seed_hi);
+    const uint32_t prio = move_priority((uint32_t)R.id[slot], k);
     const uint32_t i = append_slot(&a.ctl->act_count[2]);
     if (i < a.act_cap) {
-      const U4 k = move_step_keys((uint32_t)t, R.seed_lo, R.seed_hi);
       MoveEntry e;
-      e.c0 = (uint32_t)cell;
+      e.c0 = ((uint32_t)y0 << 16) | (uint32_t)x0;
       e.ref = ((uint32_t)rep << 24) | (uint32_t)slot;
-      e.prio = move_priority((uint32_t)R.id[slot], k);
-      e.info = (uint32_t)fp | ex | ((uint32_t)(dx + 8) << MV_DX) | ((uint32_t)(dy + 8) << MV_DY);
+      e.prio = prio;
+      e.info = (uint32_t)fp | ex | ((uint32_t)(dx + 8) << MV_DX) | ((uint32_t)(dy + 8) << MV_DY) |
+               ((uint32_t)fin << MV_FIN) | (gone ? MV_GONE : 0u);
       a.act[2][i] = e;
     }
   }
@@ -189,7 +256,7 @@ __device__ __forceinline__ void foot_cells(const PathTab* tab, uint32_t xy, cons
     const int x = x0 + (s == 0 ? 0 : (int)tab->d[i0 + s - 1][0]);
     const int y = y0 + (s == 0 ? 0 : (int)tab->d[i0 + s - 1][1]);
     c[s] = y * R.W + x;
-    q[s] = ((((y >> 4) * R.claim_tx) + (x >> 4)) << 8) | ((y & 15) << 4) | (x & 15);
+    q[s] = claim_index(R, x, y);
   }
 }
 
@@ -235,44 +302,85 @@ __device__ __forceinline__ void commit_move(const StepArgs& a, const RepDev& R, 
   }
 }
 
-// Claim value: an 8-bit round tag (255 for the first round of an epoch, one
-// less each round) above the 24-bit priority, so a claim of a later round
-// always wins atomicMin over an older one of the same epoch.  Claims are
-// cleared at the end of the step, and an epoch that runs out of tags is
-// closed the same way before claims start again at 255.
-__device__ __forceinline__ uint32_t claim_of(int tag_round, uint32_t prio) {
-  return ((uint32_t)(255 - tag_round) << 24) | prio;
+// First-round move of an agent that owns its footprint: nobody has touched
+// the footprint this step, so the outcome the movement-order pass recorded
+// holds, and only occupancy bits change.
+__device__ __forceinline__ void commit_first(const StepArgs& a, const RepDev& R, int rep, int slot,
+                                             const int* c, uint32_t info) {
+  const int fin = (int)((info >> MV_FIN) & 7u);
+  const bool gone = (info & MV_GONE) != 0u;
+  if (fin == 0) return;
+  int cf = c[0];
+#pragma unroll
+  for (int s = 1; s <= 5; ++s)
+    if (s == fin) cf = c[s];
+  atomicAnd(&R.rec[c[0]], ~(REC_OCC | REC_STA));
+  if (gone) {
+    R.cell[slot] = -1;
+    atomicAdd(&a.exited[rep], 1);
+  } else {
+    atomicOr(&R.rec[cf], REC_OCC);
+    R.cell[slot] = cf;
+  }
 }
 
-constexpr int kTagRounds = 250;  // rounds per claim epoch before a clean-up
+// A block's waiting movers: fields by mover, and the two index lists used in
+// turn by the rounds (in shared memory or in the block's global slice).
+struct MoverLists {
+  uint32_t *P, *C0, *RF, *IN, *L0, *L1;
+  __device__ __forceinline__ uint32_t* list(int i) const { return i ? L1 : L0; }
+};
+
+__device__ __forceinline__ MoverLists smem_lists(unsigned char* dsm) {
+  MoverLists m;
+  m.P = reinterpret_cast<uint32_t*>(dsm);
+  m.C0 = m.P + kMoveSmemCap;
+  m.RF = m.C0 + kMoveSmemCap;
+  m.IN = m.RF + kMoveSmemCap;
+  m.L0 = m.IN + kMoveSmemCap;
+  m.L1 = m.L0 + kMoveSmemCap;
+  return m;
+}
+
+// Claims of round tag g for the movers of a list (waiting movers that lost
+// theirs when the claim arrays were cleared).
+__device__ __forceinline__ void claim_list(const StepArgs& a, const PathTab* tab,
+                                           const MoverLists& ml, const uint32_t* list,
+                                           uint32_t n, uint32_t g) {
+  for (uint32_t k = threadIdx.x; k < n; k += blockDim.x) {
+    const uint32_t idx = list[k];
+    const uint32_t info = ml.IN[idx];
+    const RepDev& R = a.reps[ml.RF[idx] >> 24];
+    int c[6], q[6];
+    foot_cells(tab, ml.C0[idx], R, info, c, q);
+    const int n_fp = (int)(info & MV_LEN);
+    const uint32_t v = claim_of(g, ml.P[idx]);
+    uint32_t* cl = R.claim[g & 1u];
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+      if (s <= n_fp) atomicMin(&cl[q[s]], v);
+  }
+}
 
 __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ PathTab tab;
   __shared__ uint32_t s_cnt[2];
+  __shared__ uint32_t s_base;
   build_path_tab(&tab);
   Ctl* ctl = a.ctl;
+  uint32_t g = __ldcg(&ctl->claim_tag);  // tag of the current round
   const uint32_t n0 = min(__ldcg(&ctl->act_count[2]), a.act_cap);
   const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const uint32_t start = (uint32_t)(((unsigned long long)n0 * b) / G);
   const uint32_t nb = (uint32_t)(((unsigned long long)n0 * (b + 1)) / G) - start;
-  const bool in_smem = (n0 + G - 1) / G <= (uint32_t)kMoveSmemCap;  // same for every block
-  uint32_t *P, *C0, *RF, *IN, *L[2];  // C0: start cell as (y << 16) | x
-  if (in_smem) {
-    P = reinterpret_cast<uint32_t*>(dsm);
-    C0 = P + kMoveSmemCap;
-    RF = C0 + kMoveSmemCap;
-    IN = RF + kMoveSmemCap;
-    L[0] = IN + kMoveSmemCap;
-    L[1] = L[0] + kMoveSmemCap;
-  } else {
-    P = a.mv_prio + start;
-    C0 = a.mv_c0 + start;
-    RF = a.mv_ref + start;
-    IN = a.mv_info + start;
-    L[0] = a.mv_list[0] + start;
-    L[1] = a.mv_list[1] + start;
-  }
+  MoverLists gl;  // the block's slice of global memory
+  gl.P = a.mv_prio + start;
+  gl.C0 = a.mv_c0 + start;
+  gl.RF = a.mv_ref + start;
+  gl.IN = a.mv_info + start;
+  gl.L0 = a.mv_list[0] + start;
+  gl.L1 = a.mv_list[1] + start;
   if (tid < 2) s_cnt[tid] = 0u;
   const unsigned long long t_start = global_ns();
   if (b == 0 && tid == 0) {
@@ -280,57 +388,159 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
     for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = 0ull;
   }
   __syncthreads();
-  // this block's movers into shared memory, then their claims for round 0
+  bool reclaim = g + 1u < kTags;  // tags left for the next round's claims
+
+  // ---- claims of round 0, straight from the step's list
   for (uint32_t k = tid; k < nb; k += blockDim.x) {
     const MoveEntry e = a.act[2][start + k];
     const RepDev& R = a.reps[e.ref >> 24];
-    P[k] = e.prio;
-    C0[k] = ((e.c0 / (uint32_t)R.W) << 16) | (e.c0 % (uint32_t)R.W);
-    RF[k] = e.ref;
-    IN[k] = e.info;
-    L[0][k] = k;
-  }
-  __syncthreads();
-  if (tid == 0) atomicMax(&ctl->phase_ns[6], global_ns() - t_start);
-  for (uint32_t k = tid; k < nb; k += blockDim.x) {
-    const RepDev& R = a.reps[RF[k] >> 24];
     int c[6], q[6];
-    foot_cells(&tab, C0[k], R, IN[k], c, q);
-    const int n = (int)(IN[k] & MV_LEN);
-    const uint32_t v = claim_of(0, P[k]);
+    foot_cells(&tab, e.c0, R, e.info, c, q);
+    const int n = (int)(e.info & MV_LEN);
+    uint32_t* cl = R.claim[g & 1u];
+    const uint32_t v = claim_of(g, e.prio);
 #pragma unroll
     for (int s = 0; s < 6; ++s)
-      if (s <= n) atomicMin(&R.claim[0][q[s]], v);
+      if (s <= n) atomicMin(&cl[q[s]], v);
   }
-  if (tid == 0) s_cnt[0] = nb;
+  if (tid == 0) atomicMax(&ctl->phase_ns[3], global_ns() - t_start);
+  if (!grid_barrier(ctl)) return;
+
+  // ---- round 0: the ones that must wait claim for round 1 and go to the
+  // block's global staging area
+  for (uint32_t k = tid; k < nb; k += blockDim.x) {
+    const MoveEntry e = a.act[2][start + k];
+    const int rep = (int)(e.ref >> 24), slot = (int)(e.ref & 0xFFFFFFu);
+    const RepDev& R = a.reps[rep];
+    int c[6], q[6];
+    foot_cells(&tab, e.c0, R, e.info, c, q);
+    const int n = (int)(e.info & MV_LEN);
+    const uint32_t* now = R.claim[g & 1u];
+    const uint32_t mine_v = claim_of(g, e.prio);
+    uint32_t cl[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) cl[s] = (s <= n) ? __ldcg(&now[q[s]]) : mine_v;
+    bool mine = true;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) mine &= (cl[s] == mine_v);
+    if (mine) {
+      commit_first(a, R, rep, slot, c, e.info);
+    } else {
+      if (reclaim) {
+        uint32_t* nxt = R.claim[(g + 1u) & 1u];
+        const uint32_t v = claim_of(g + 1u, e.prio);
+#pragma unroll
+        for (int s = 0; s < 6; ++s)
+          if (s <= n) atomicMin(&nxt[q[s]], v);
+      }
+      const uint32_t j = append_slot(&s_cnt[1]);
+      gl.P[j] = e.prio;
+      gl.C0[j] = e.c0;
+      gl.RF[j] = e.ref;
+      gl.IN[j] = e.info;
+    }
+  }
   __syncthreads();
-  if (tid == 0) atomicMax(&ctl->phase_ns[0], global_ns() - t_start);
+  const uint32_t w0 = s_cnt[1];
+  // the waiting movers to shared memory when they fit (a block's choice)
+  const bool in_smem = w0 <= (uint32_t)kMoveSmemCap;
+  MoverLists ml = in_smem ? smem_lists(dsm) : gl;
+  for (uint32_t k = tid; k < w0; k += blockDim.x) {
+    if (in_smem) {
+      ml.P[k] = gl.P[k];
+      ml.C0[k] = gl.C0[k];
+      ml.RF[k] = gl.RF[k];
+      ml.IN[k] = gl.IN[k];
+    }
+    ml.L1[k] = k;
+  }
+  if (tid == 0 && w0) atomicAdd(&ctl->wait_count[1], w0);
+  if (tid == 0) {
+    atomicMax(&ctl->phase_ns[0], global_ns() - t_start);
+    atomicMax(&ctl->phase_ns[4], (unsigned long long)nb);
+    atomicMax(&ctl->phase_ns[5], (unsigned long long)w0);
+  }
   if (!grid_barrier(ctl)) return;
   if (tid == 0) atomicMax(&ctl->phase_ns[1], global_ns() - t_start);
-  int r = 0, tr = 0;  // round of the step, round within the claim epoch
-  for (;;) {
-    // every agent still waiting checks its claims of round r (array r&1),
-    // moves if it holds all its cells, else claims for round r+1
+  uint32_t waiting = __ldcg(&ctl->wait_count[1]);
+  if (b == 0 && tid == 0) {
+    ctl->round_n[0] = waiting;
+    ctl->round_ns[1] = global_ns();
+  }
+  int r = 1;
+  bool single = (G == 1);
+  while (waiting > 0) {
     const int in_l = r & 1, out_l = (r + 1) & 1;
+    if (!reclaim) {
+      // out of tags: clear every claim, then the waiting movers claim again
+      // with the first tag
+      __syncthreads();
+      clear_all_claims(a, single);
+      if (!round_barrier(ctl, single)) return;
+      g = 0u;
+      claim_list(a, &tab, ml, ml.list(in_l), s_cnt[in_l], 0u);
+      if (!round_barrier(ctl, single)) return;
+    } else {
+      ++g;
+    }
+    if (!single && waiting <= (uint32_t)kTail) {
+      // hand every waiting mover to block 0, which finishes alone
+      const uint32_t n_it = s_cnt[in_l];
+      if (tid == 0) s_base = n_it ? atomicAdd(&ctl->tail_count, n_it) : 0u;
+      __syncthreads();
+      const uint32_t* lin = ml.list(in_l);
+      for (uint32_t k = tid; k < n_it; k += blockDim.x) {
+        const uint32_t idx = lin[k];
+        MoveEntry e;
+        e.c0 = ml.C0[idx];
+        e.ref = ml.RF[idx];
+        e.prio = ml.P[idx];
+        e.info = ml.IN[idx];
+        a.act[0][s_base + k] = e;
+      }
+      if (!grid_barrier(ctl)) return;
+      if (b != 0) return;
+      const uint32_t nt = __ldcg(&ctl->tail_count);
+      ml = smem_lists(dsm);
+      uint32_t* lt = ml.list(in_l);
+      for (uint32_t k = tid; k < nt; k += blockDim.x) {
+        const MoveEntry e = a.act[0][k];
+        ml.P[k] = e.prio;
+        ml.C0[k] = e.c0;
+        ml.RF[k] = e.ref;
+        ml.IN[k] = e.info;
+        lt[k] = k;
+      }
+      if (tid == 0) {
+        s_cnt[in_l] = nt;
+        ctl->phase_ns[6] = (unsigned long long)r;
+      }
+      single = true;
+      __syncthreads();
+    }
+    // every agent still waiting checks its claims of tag g, moves if it
+    // holds all its cells, else claims with tag g+1
+    reclaim = g + 1u < kTags;
     if (b == 0 && tid == 0) ctl->wait_count[(r + 2) % 3] = 0u;
     const uint32_t n_it = s_cnt[in_l];
     __syncthreads();
     if (tid == 0) s_cnt[out_l] = 0u;
     __syncthreads();
     const unsigned long long t_round = global_ns();
-    const bool new_epoch = (tr + 1 >= kTagRounds);
+    const uint32_t* lin = ml.list(in_l);
+    uint32_t* lout = ml.list(out_l);
     for (uint32_t k = tid; k < n_it; k += blockDim.x) {
-      const uint32_t idx = L[in_l][k];
-      const uint32_t info = IN[idx];
-      const uint32_t ref = RF[idx];
-      const uint32_t p = P[idx];
+      const uint32_t idx = lin[k];
+      const uint32_t info = ml.IN[idx];
+      const uint32_t ref = ml.RF[idx];
+      const uint32_t p = ml.P[idx];
       const int rep = (int)(ref >> 24), slot = (int)(ref & 0xFFFFFFu);
       const RepDev& R = a.reps[rep];
       int c[6], q[6];
-      foot_cells(&tab, C0[idx], R, info, c, q);
+      foot_cells(&tab, ml.C0[idx], R, info, c, q);
       const int n = (int)(info & MV_LEN);
-      const uint32_t* now = R.claim[in_l];
-      const uint32_t mine_v = claim_of(tr, p);
+      const uint32_t* now = R.claim[g & 1u];
+      const uint32_t mine_v = claim_of(g, p);
       uint32_t cl[6];
 #pragma unroll
       for (int s = 0; s < 6; ++s) cl[s] = (s <= n) ? __ldcg(&now[q[s]]) : mine_v;
@@ -344,79 +554,39 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
         for (int s = 0; s < 6; ++s) pr[s] = (s <= wl) ? __ldcg(&R.rec[c[s]]) : REC_OCC;
         commit_move(a, R, rep, slot, c, pr);
       } else {
-        if (!new_epoch) {
-          uint32_t* nxt = R.claim[out_l];
-          const uint32_t v = claim_of(tr + 1, p);
+        if (reclaim) {
+          uint32_t* nxt = R.claim[(g + 1u) & 1u];
+          const uint32_t v = claim_of(g + 1u, p);
 #pragma unroll
           for (int s = 0; s < 6; ++s)
             if (s <= n) atomicMin(&nxt[q[s]], v);
         }
-        L[out_l][append_slot(&s_cnt[out_l])] = idx;
+        lout[append_slot(&s_cnt[out_l])] = idx;
       }
     }
     __syncthreads();
-    if (tid == 0 && r < 2) atomicMax(&ctl->phase_ns[2 + r], global_ns() - t_round);
-    if (tid == 0 && r < 2) atomicMax(&ctl->phase_ns[4 + r], (unsigned long long)n_it);
-    if (tid == 0 && s_cnt[out_l]) atomicAdd(&ctl->wait_count[(r + 1) % 3], s_cnt[out_l]);
-    if (!grid_barrier(ctl)) return;
-    const uint32_t waiting = __ldcg(&ctl->wait_count[(r + 1) % 3]);
+    if (tid == 0 && r == 1) atomicMax(&ctl->phase_ns[2], global_ns() - t_round);
+    if (single) {
+      __threadfence_block();
+      waiting = s_cnt[out_l];
+    } else {
+      if (tid == 0 && s_cnt[out_l]) atomicAdd(&ctl->wait_count[(r + 1) % 3], s_cnt[out_l]);
+      if (!grid_barrier(ctl)) return;
+      waiting = __ldcg(&ctl->wait_count[(r + 1) % 3]);
+    }
     if (b == 0 && tid == 0 && r < kRoundLog) {
       ctl->round_n[r] = waiting;
       ctl->round_ns[r + 1] = global_ns();
     }
     ++r;
-    ++tr;
-    if (waiting == 0) break;
     if (r > (int)n0 + 1) {
       if (b == 0 && tid == 0) atomicCAS(&ctl->err, 0, kDevErrRounds);
       return;
     }
-    if (new_epoch) {
-      // out of tags: clear every claim of this step's movers, then the
-      // agents still waiting claim again with the first tag of a new epoch
-      for (uint32_t k = tid; k < nb; k += blockDim.x) {
-        const RepDev& R = a.reps[RF[k] >> 24];
-        int c[6], q[6];
-        foot_cells(&tab, C0[k], R, IN[k], c, q);
-        const int n = (int)(IN[k] & MV_LEN);
-#pragma unroll
-        for (int s = 0; s < 6; ++s)
-          if (s <= n) {
-            __stcg(&R.claim[0][q[s]], 0xFFFFFFFFu);
-            __stcg(&R.claim[1][q[s]], 0xFFFFFFFFu);
-          }
-      }
-      if (!grid_barrier(ctl)) return;
-      tr = 0;
-      const int nl = r & 1;
-      for (uint32_t k = tid; k < s_cnt[nl]; k += blockDim.x) {
-        const uint32_t idx = L[nl][k];
-        const RepDev& R = a.reps[RF[idx] >> 24];
-        int c[6], q[6];
-        foot_cells(&tab, C0[idx], R, IN[idx], c, q);
-        const int n = (int)(IN[idx] & MV_LEN);
-        const uint32_t v = claim_of(0, P[idx]);
-#pragma unroll
-        for (int s = 0; s < 6; ++s)
-          if (s <= n) atomicMin(&R.claim[nl][q[s]], v);
-      }
-      if (!grid_barrier(ctl)) return;
-    }
-  }
-  // clear this step's claims: every mover's footprint cells, both arrays
-  for (uint32_t k = tid; k < nb; k += blockDim.x) {
-    const RepDev& R = a.reps[RF[k] >> 24];
-    int c[6], q[6];
-    foot_cells(&tab, C0[k], R, IN[k], c, q);
-    const int n = (int)(IN[k] & MV_LEN);
-#pragma unroll
-    for (int s = 0; s < 6; ++s)
-      if (s <= n) {
-        __stcg(&R.claim[0][q[s]], 0xFFFFFFFFu);
-        __stcg(&R.claim[1][q[s]], 0xFFFFFFFFu);
-      }
   }
   if (b == 0 && tid == 0) {
+    // the next step's first claims use a tag below every one used so far
+    ctl->claim_tag = min(g + 1u, kTags);
     ctl->movers_total += (unsigned long long)n0;
     ctl->rounds_last = r;
     ctl->rounds_total += (unsigned long long)r;
@@ -453,6 +623,7 @@ __device__ __forceinline__ void reset_step_counters(Ctl* c) {
     c->act_count[i] = 0u;
     c->wait_count[i] = 0u;
   }
+  c->tail_count = 0u;
 }
 
 __global__ void k_step_begin(StepArgs a) {
@@ -466,8 +637,12 @@ __global__ void k_step_end(StepArgs a) {
   }
 }
 
+// Queues three kernels: the claim clean-up check, its bookkeeping, and the
+// movement-order pass.
 int move_prep_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s) {
   if (ch.n <= 0) return 0;
+  k_claim_epoch<<<grid, 256, 0, s>>>(a);
+  k_claim_epoch_done<<<1, 32, 0, s>>>(a);
   k_move_prep<<<grid, 256, 0, s>>>(a, ch);
   return 0;
 }

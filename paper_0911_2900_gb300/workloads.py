@@ -109,6 +109,15 @@ def add_obstacles(t: np.ndarray, fraction: float, rng: np.random.Generator,
                 break
 
 
+def exit_apron(t: np.ndarray, depth: int = 3) -> np.ndarray:
+    """Bool mask of the cells within `depth` (Chebyshev) of an exit cell, for
+    add_obstacles' `protect`, so that no rectangle walls an exit in."""
+    from scipy import ndimage
+
+    return ndimage.binary_dilation(t == EXIT, structure=np.ones((3, 3), bool),
+                                   iterations=depth)
+
+
 def seal_unreachable(t: np.ndarray) -> int:
     """Turns every free cell that no 8-connected walk through non-wall cells
     links to an exit into a wall; returns how many cells were sealed."""
@@ -264,7 +273,7 @@ def config_batch(n_rep=256, seed=0, cells_lo=100 ** 2, cells_hi=2000 ** 2,
         H = max(16, int(round(cells / W)))
         t = room(W, H)
         spread_exits(t, int(rng.integers(1, 5)), 4)
-        add_obstacles(t, 0.10, np.random.default_rng(seed * 1000 + r + 1))
+        add_obstacles(t, 0.10, np.random.default_rng(seed * 1000 + r + 1), protect=exit_apron(t))
         seal_unreachable(t)
         free = int((t == FREE).sum())
         n = int(math.exp(rng.uniform(math.log(agents_lo), math.log(agents_hi))))

@@ -32,11 +32,14 @@ def fg():
 
 
 def run_gpu(fg, works, steps, precision="fp32_recheck", reach="l2", digests=True, resort=8,
-            graph=True, id_perm=None, start_step=0, lanes=None, tile_shift=None):
+            graph=True, id_perm=None, start_step=0, lanes=None, tile_shift=None, chunks=None,
+            graph_steps=None, tune=None):
     ctx = fg.Context(len(works), precision, reach)
     ctx.set_option("digests", 1 if digests else 0)
     ctx.set_option("resort_period", resort)
     ctx.set_option("use_graph", 1 if graph else 0)
+    if graph_steps is not None:
+        ctx.set_option("graph_steps", graph_steps)
     if tile_shift is not None:
         ctx.set_option("tile_shift", tile_shift)
     if lanes is not None:
@@ -48,7 +51,13 @@ def run_gpu(fg, works, steps, precision="fp32_recheck", reach="l2", digests=True
             ctx.place(r, w.cells, start_step=start_step)
         else:
             ctx.place(r, w.cells[id_perm], ids=id_perm.astype(np.int32), start_step=start_step)
-    ctx.step(steps)
+    done = 0
+    for n in (chunks or [steps]):
+        if tune is not None and done == tune:
+            ctx.tune_report = ctx.autotune(trials=2)
+        ctx.step(n)
+        done += n
+    assert done == steps
     out = []
     for r, w in enumerate(works):
         cells, des, st = ctx.readback(r, len(w.cells))
@@ -166,6 +175,71 @@ def test_storage_order_graph_and_resort_do_not_matter(fg, orc):
         assert_same(g, o, steps)
 
 
+def test_step_loop_graph_modes(fg, orc):
+    """The step loop as one captured graph per call, one graph per step,
+    direct launches, and calls that start at every phase of the re-sort
+    period all give the oracle's trajectories."""
+    w = wl.config_small_room(W=90, H=70, n=1800, seed=12, v_m=3)
+    steps = 29
+    o = run_oracle(orc, w, steps)
+    for kw in (dict(), dict(graph_steps=1), dict(graph=False),
+               dict(chunks=[3, 5, 1, 7, 2, 11]), dict(chunks=[1] * 29, graph_steps=0),
+               dict(chunks=[13, 13, 3])):
+        _, (g,) = run_gpu(fg, [w], steps, "fp32_recheck", **kw)
+        assert_same(g, o, steps)
+
+
+@pytest.mark.parametrize("reserve,tag", [(0, 240), (254, None), (96, None), (96, 200)])
+def test_claim_tag_cleanups(fg, orc, reserve, tag):
+    """Movement claims whose tags run out within a step (cleared by the
+    rounds kernel), before every step, or every few steps: same
+    trajectories."""
+    w = wl.config_small_room(W=70, H=70, n=2200, seed=21, v_m=5)
+    steps = 20
+    o = run_oracle(orc, w, steps)
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.set_option("digests", 1)
+    ctx.set_option("claim_reserve", reserve)
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx.place(0, w.cells)
+    for i in range(steps):
+        if tag is not None:
+            ctx.set_option("claim_tag", tag)
+        ctx.step(1)
+    cells, des, st = ctx.readback(0, len(w.cells))
+    dc, dd = ctx.digests(0, steps)
+    assert_same(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd), o, steps)
+
+
+def test_autotune_changes_speed_not_results(fg, orc):
+    """Tuning in the middle of a run (re-sort bucket side and the planning
+    variant of every v_m present) leaves the trajectories bit-exact."""
+    works = wl.config_batch(n_rep=5, seed=11, cells_hi=250 ** 2, agents_hi=5000)
+    steps = 24
+    ctx, gs = run_gpu(fg, works, steps, "fp32_recheck", chunks=[10, 14], tune=10)
+    rep = ctx.tune_report
+    assert rep["tile_shift"] in (3, 4, 5, 6)
+    for w in works:
+        assert rep["lanes"][w.v_m - 1] in (0, 1, 2, 4, 8)
+        assert len(rep["lanes_us"][w.v_m]) == 5
+    for w, g in zip(works, gs):
+        assert_same(g, run_oracle(orc, w, steps), steps)
+
+
+def test_autotune_cache_roundtrip(fg, tmp_path):
+    w = wl.config_small_room(W=60, H=60, n=500, seed=2, v_m=2)
+    cache = str(tmp_path / "tune.json")
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx.place(0, w.cells)
+    first = ctx.autotune(trials=1, cache=cache, key="room60")
+    second = ctx.autotune(trials=1, cache=cache, key="room60")
+    assert not first["cached"] and second["cached"]
+    assert second["lanes"] == first["lanes"] and second["tile_shift"] == first["tile_shift"]
+    with pytest.raises(fg.FastError):
+        ctx.autotune(trials=0)
+
+
 def test_batched_replicates(fg, orc):
     works = wl.config_batch(n_rep=6, seed=3, cells_hi=300 ** 2, agents_hi=6000)
     steps = 30
@@ -241,6 +315,37 @@ def test_invalid_inputs_are_rejected(fg):
 
 
 # --------------------------------------------------------------------------- full size
+def test_batched_form_full_size_sampled(fg, orc):
+    """256 replicates of the batched form (grids 100^2..2000^2 cells, 1e3..1e5
+    agents, v_m 1..5) in one context, autotuned, the step loop as one graph:
+    after 8 steps, replicates sampled across sizes and every v_m match the
+    oracle run from the same start for all 8 steps, and every replicate keeps
+    the conservation invariants."""
+    works = wl.config_batch()
+    steps = 8
+    ctx = fg.Context(len(works), "fp32_recheck")
+    ctx.set_option("digests", 1)
+    for r, w in enumerate(works):
+        ctx.init_grid(r, w.cell_type, w.k_S, w.v_m, w.seed)
+        ctx.place(r, w.cells)
+    ctx.autotune(trials=2)
+    ctx.step(steps)
+    order = np.argsort([len(w.cells) for w in works])
+    sample = {int(order[0]), int(order[len(order) // 2]), int(order[-1])}
+    for v in range(1, 6):
+        sample.add(next(r for r, w in enumerate(works) if w.v_m == v))
+    for r, w in enumerate(works):
+        cells, _, st = ctx.readback(r, len(w.cells))
+        alive = cells >= 0
+        assert st["alive"] + st["exited"] == len(w.cells) and st["alive"] == int(alive.sum())
+        assert len(np.unique(cells[alive])) == int(alive.sum())
+        assert (w.cell_type.ravel()[cells[alive]] == wl.FREE).all()
+        if r in sample:
+            dc, dd = ctx.digests(r, steps)
+            o = run_oracle(orc, w, steps, threads=os.cpu_count() or 1)
+            assert np.array_equal(dd, o["dig_des"]) and np.array_equal(dc, o["dig_cell"]), r
+            assert np.array_equal(cells, o["cells"]), r
+
 def test_precision_form_full_size_one_step(fg, orc):
     """4000x4000, 1M clustered agents, v_m=4, FP32 + FP64 re-check, in the
     launch configuration the benchmark times: after 3 steps, the next step's
