@@ -512,7 +512,12 @@ def bench_ours(args):
         if tune is not None:
             cfg["autotuned"] = {"tile_shift": tune["tile_shift"],
                                 "lanes_by_v": {str(v + 1): l for v, l in enumerate(tune["lanes"])
-                                               if l >= 0}}
+                                               if l >= 0},
+                                "plan_us_by_v_and_lanes": {
+                                    str(v): {str(l): round(us, 1) for l, us in d.items()}
+                                    for v, d in tune["lanes_us"].items()},
+                                "plan_us_by_tile_shift": {str(k): round(us, 1) for k, us
+                                                          in tune["shift_us"].items()}}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,

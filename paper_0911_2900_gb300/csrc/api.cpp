@@ -405,7 +405,7 @@ int enqueue_plan(fast_ctx* c, const StepArgs& a, bool diag, bool events) {
   }
   if (events) CUDA_TRY(c, record_event(c, 1));
   if (c->precision == FAST_FP32_RECHECK && !diag)
-    LAUNCH_TRY(c, plan_recheck_launch(a, std::max(1, c->sms * 4), c->cur));
+    LAUNCH_TRY(c, plan_recheck_launch(a, std::max(1, c->sms * 16), c->cur));
   return FAST_OK;
 }
 

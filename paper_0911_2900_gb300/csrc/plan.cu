@@ -17,19 +17,32 @@ int diag_launch_v4(const StepArgs&, int, const Chunks&, int, cudaStream_t);
 int diag_launch_v5(const StepArgs&, int, const Chunks&, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// FP64 re-check of the queued agents: 8 lanes per agent compute the FP64
-// weights of candidates k = l, l+8, ... (independent, so their latency
-// overlaps), then lane 0 of the group forms W and the cumulative sums
-// sequentially in canonical order, exactly as the FP64 rule does.
-constexpr int kRcLanes = 8;
-constexpr int kRcPerBlock = 128 / kRcLanes;
+// FP64 re-check of the queued agents, kRcAgents agents per block of 256
+// threads.  The threads share out all FP64 weights of the block's agents (the
+// flattened list of (agent, candidate) pairs, about one exp64 per thread, so
+// their long FP64 latencies overlap and every FP64 instruction is full), then
+// thread i forms agent i's cumulative sums C_k sequentially in canonical
+// order, exactly as the FP64 rule does (W is the last of them: the same
+// additions in the same order), and finds the first k with fl(u*W) < C_k by
+// comparing bit patterns (order-preserving for non-negative doubles).
+constexpr int kRcThreads = 256;
+constexpr int kRcAgents = 8;
 
-__global__ void __launch_bounds__(128) k_recheck(StepArgs a) {
+struct RcAgent {
+  unsigned long long m0, m1;
+  double S0, nks;
+  const uint32_t* rec;
+  int cell, W, v, pad;
+};
+
+__global__ void __launch_bounds__(kRcThreads) k_recheck(StepArgs a) {
   __shared__ int8_t s_tab[5][kMaxK][2];
   __shared__ int s_K[5];
-  __shared__ double s_w[kRcPerBlock][kMaxK];
+  __shared__ int s_first[kRcAgents + 1];  // prefix of the agents' candidate counts
+  __shared__ RcAgent s_ag[kRcAgents];
+  __shared__ double s_c[kRcAgents][kMaxK];  // weights, then C_k
   const uint32_t n = min(a.ctl->q_count, a.q_cap);
-  if ((uint32_t)blockIdx.x * kRcPerBlock >= n) return;
+  if ((uint32_t)blockIdx.x * kRcAgents >= n) return;
   const int reach = a.reps[0].reach;  // one reach set per context
   if (threadIdx.x < 5) {
     const int v = threadIdx.x + 1;
@@ -44,62 +57,91 @@ __global__ void __launch_bounds__(128) k_recheck(StepArgs a) {
     s_K[v - 1] = k;
   }
   __syncthreads();
-  const int g = threadIdx.x / kRcLanes, l = threadIdx.x % kRcLanes;
+  const int tid = threadIdx.x;
   const int t = a.ctl->t;
-  for (uint32_t base = blockIdx.x * kRcPerBlock; base < n; base += gridDim.x * kRcPerBlock) {
-    const uint32_t q = base + g;
-    const bool valid = q < n;
-    int rep = 0, slot = 0, cell = 0, K = 0, v = 1, W = 0;
+  for (uint32_t q0 = blockIdx.x * kRcAgents; q0 < n; q0 += gridDim.x * kRcAgents) {
+    // thread i < kRcAgents: agent q0 + i
+    const bool mine = tid < kRcAgents && q0 + tid < n;
+    int rep = 0, slot = 0, K = 0;
     uint32_t rec0 = 0;
-    double* w = s_w[g];
-    if (valid) {
-      const uint32_t e = a.queue[q];
+    if (mine) {
+      const uint32_t e = a.queue[q0 + tid];
       rep = (int)(e >> 24);
       slot = (int)(e & 0xFFFFFFu);
       const RepDev& R = a.reps[rep];
-      cell = R.cell[slot];
-      v = R.v;
-      W = R.W;
-      K = s_K[v - 1];
-      rec0 = R.rec[cell];
-      const double S0 = s64_of(rec0);
-      const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
-      const unsigned long long m1 = (R.mw > 1) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
-      const double nks = -R.kS;
-      for (int k = l; k < K; k += kRcLanes) {
-        double wk = 0.0;
-        if (mask_bit(m0, m1, k)) {
-          const int dx = s_tab[v - 1][k][0], dy = s_tab[v - 1][k][1];
-          const bool center = (dx == 0 && dy == 0);
-          const uint32_t r = center ? rec0 : R.rec[cell + dy * W + dx];
-          if (center || !(r & REC_OCC)) wk = exp64(__dmul_rn(nks, __dsub_rn(s64_of(r), S0)));
-        }
-        w[k] = wk;
-      }
+      RcAgent x;
+      x.cell = R.cell[slot];
+      x.W = R.W;
+      x.v = R.v;
+      x.rec = R.rec;
+      rec0 = R.rec[x.cell];
+      x.S0 = s64_of(rec0);
+      x.nks = -R.kS;
+      x.m0 = R.mask[(size_t)x.cell * R.mw];
+      x.m1 = (R.mw > 1) ? R.mask[(size_t)x.cell * R.mw + 1] : 0ull;
+      x.pad = 0;
+      s_ag[tid] = x;
+      K = s_K[x.v - 1];
     }
-    __syncwarp();
-    if (valid && l == 0) {
+    if (tid < 32) {
+      int incl = K;  // lanes >= kRcAgents hold 0
+#pragma unroll
+      for (int o = 1; o < kRcAgents; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (tid >= o) incl += y;
+      }
+      if (tid < kRcAgents) s_first[tid + 1] = incl;
+      if (tid == 0) s_first[0] = 0;
+    }
+    __syncthreads();
+    const int total = s_first[kRcAgents];
+    // every FP64 weight of the block's agents
+    for (int idx = tid; idx < total; idx += kRcThreads) {
+      int i = 0;
+#pragma unroll
+      for (int step = kRcAgents / 2; step > 0; step >>= 1)
+        if (s_first[i + step] <= idx) i += step;
+      const int k = idx - s_first[i];
+      const RcAgent& x = s_ag[i];
+      double wk = 0.0;
+      if (mask_bit(x.m0, x.m1, k)) {
+        const int dx = s_tab[x.v - 1][k][0], dy = s_tab[x.v - 1][k][1];
+        const bool center = (dx == 0 && dy == 0);
+        const uint32_t r = x.rec[x.cell + dy * x.W + dx];
+        if (center || !(r & REC_OCC)) wk = exp64(__dmul_rn(x.nks, __dsub_rn(s64_of(r), x.S0)));
+      }
+      s_c[i][k] = wk;
+    }
+    __syncthreads();
+    if (mine) {
+      // C_k in canonical order over the positive weights (a zero weight is
+      // marked -1 and never chosen); W = the last C
+      double* ci = s_c[tid];
+      double acc = 0.0;
+      for (int k = 0; k < K; ++k) {
+        const double wk = ci[k];
+        const bool pos = __double_as_longlong(wk) != 0ll;
+        if (pos) acc = __dadd_rn(acc, wk);
+        ci[k] = pos ? acc : -1.0;
+      }
       const RepDev& R = a.reps[rep];
-      double Wsum = 0.0;
-      for (int k = 0; k < K; ++k)
-        if (w[k] > 0.0) Wsum = __dadd_rn(Wsum, w[k]);
       const double u = plan_uniform((uint32_t)R.id[slot], (uint32_t)t, R.seed_lo, R.seed_hi);
-      const double r = __dmul_rn(u, Wsum);
-      double c = 0.0;
+      const long long rb = __double_as_longlong(__dmul_rn(u, acc));
       int chosen = -1, last = -1;
       for (int k = 0; k < K; ++k) {
-        if (w[k] > 0.0) {
-          c = __dadd_rn(c, w[k]);
-          if (chosen < 0 && r < c) chosen = k;
+        const long long cb = __double_as_longlong(ci[k]);
+        if (cb >= 0) {
+          if (chosen < 0 && rb < cb) chosen = k;
           last = k;
         }
       }
+      const RcAgent& x = s_ag[tid];
       const int kk = chosen >= 0 ? chosen : last;
-      const int target = cell + s_tab[v - 1][kk][1] * W + s_tab[v - 1][kk][0];
+      const int target = x.cell + s_tab[x.v - 1][kk][1] * x.W + s_tab[x.v - 1][kk][0];
       R.desired[slot] = target;
-      set_static(R.rec, cell, rec0, target == cell);
+      set_static(R.rec, x.cell, rec0, target == x.cell);
     }
-    __syncwarp();
+    __syncthreads();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.ctl->rechecked_total, (unsigned long long)n);
 }
@@ -118,7 +160,7 @@ int plan_groups_launch(const StepArgs& a, int v, int reach, int lanes, int preci
 }
 
 int plan_recheck_launch(const StepArgs& a, int grid, cudaStream_t s) {
-  k_recheck<<<grid, 128, 0, s>>>(a);
+  k_recheck<<<grid, kRcThreads, 0, s>>>(a);
   return 0;
 }
 

@@ -3,6 +3,7 @@
 // (Kretz, Sec. 1: the planning phase only reads data common to all agents;
 // Sec. 2: k_S = 1.2, k_other = 0).
 //
+//   k_plan_tile<V,REACH>    one thread per agent, per-warp record tiles
 //   k_plan_fp32<V,REACH,G>  G lanes per agent; FP32 weights exp(-k_S dS) on
 //                           the SFU, shuffle prefix sums over the G lanes,
 //                           Philox draw, margin test; draws that fall within
@@ -66,6 +67,75 @@ __device__ __forceinline__ bool mask_bit(unsigned long long m0, unsigned long lo
 
 __device__ __forceinline__ void set_static(uint32_t* rec, int cell, uint32_t rec0, bool stays) {
   rec[cell] = stays ? (rec0 | REC_STA) : (rec0 & ~REC_STA);
+}
+
+// The same as an atomic bit update (no dependence on an earlier read).
+__device__ __forceinline__ void set_static_red(uint32_t* rec, int cell, bool stays) {
+  if (stays)
+    atomicOr(&rec[cell], REC_STA);
+  else
+    atomicAnd(&rec[cell], ~REC_STA);
+}
+
+// Offsets of a reach set packed as (dx + 16) | (dy + 16) << 8, canonical order.
+template <int V, int REACH>
+__device__ __forceinline__ void fill_dxdy(int* s_dxdy) {
+  constexpr ReachTable<V, REACH> T{};
+  constexpr int K = reach_count(V, REACH);
+  for (int k = threadIdx.x; k < K; k += blockDim.x)
+    s_dxdy[k] = (T.dx[k] + 16) | ((T.dy[k] + 16) << 8);
+}
+
+// FP32 weight of a candidate record seen from (a0, b0): 0 if blocked.
+__device__ __forceinline__ float rec_weight(uint32_t r, int a0, int b0, float c32) {
+  return (r & REC_OCC) ? 0.f : ex2_approx(ds32(rec_a(r) - a0, rec_b(r) - b0) * c32);
+}
+
+// Shared end of the one-thread kernels: the draw against the cumulative
+// weights w(k) (first k with r < C_k; zero weights leave C unchanged and so
+// are never first; no such k only through rounding, which the FP64 rule then
+// settles), the margin test, and the outputs.
+template <int K, int CENTER, bool DIAG, typename WF>
+__device__ __forceinline__ void finish_g1(const StepArgs& a, const RepDev& R, int rep, int slot,
+                                          int cell, float Wt, float u, int norecheck,
+                                          const int* s_dxdy, WF w) {
+  const float r = __fmul_rn(u, Wt);
+  float cacc = 0.f, cprev = 0.f, ck = 0.f;
+  int found = -1;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const float cn = cacc + w(k);
+    const bool hit = (found < 0) && (r < cn);
+    found = hit ? k : found;
+    cprev = hit ? cacc : cprev;
+    ck = hit ? cn : ck;
+    cacc = cn;
+  }
+  if (DIAG) {
+    float* dp = a.diag_p32 + (a.diag_base[rep] + slot) * (int64_t)kMaxK;
+    float cc = 0.f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      cc = cc + w(k);
+      dp[k] = cc / Wt;
+    }
+  }
+  const float mw = R.margin * Wt;
+  const bool ok = (found >= 0) && (r > cprev + mw) && (r < ck - mw);
+  const int dd = s_dxdy[found >= 0 ? found : CENTER];
+  const int target = cell + ((dd >> 8) - 16) * R.W + ((dd & 0xFF) - 16);
+  if (DIAG) {
+    const int64_t di = a.diag_base[rep] + slot;
+    a.diag_choice32[di] = target;
+    a.diag_flag[di] = ok ? 0 : 1;
+  }
+  if (ok || norecheck) {
+    R.desired[slot] = target;
+    set_static_red(R.rec, cell, target == cell);
+  } else {
+    const uint32_t qi = append_slot(&a.ctl->q_count);
+    if (qi < a.q_cap) a.queue[qi] = ((uint32_t)rep << 24) | (uint32_t)slot;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -234,7 +304,7 @@ constexpr size_t kTileSmem = (size_t)kTileWarps * kTileH * kTileP * 4;
 template <int V, int REACH, bool DIAG, bool TILE>
 __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, int rep, int slot,
                                             int cell, const uint32_t* p0, int pitch, int t,
-                                            int norecheck) {
+                                            int norecheck, const int* s_dxdy) {
   constexpr int K = reach_count(V, REACH);
   constexpr int CENTER = reach_center<V, REACH>();
   constexpr ReachTable<V, REACH> T{};
@@ -255,77 +325,24 @@ __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, 
   float Wt = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    float wk = 0.f;
-    if (k == CENTER)
-      wk = 1.0f;
-    else if (!(rr[k] & REC_OCC))
-      wk = ex2_approx(ds32(rec_a(rr[k]) - a0, rec_b(rr[k]) - b0) * c32);
+    const float wk = (k == CENTER) ? 1.0f : rec_weight(rr[k], a0, b0, c32);
     w[k] = wk;
     Wt += wk;
   }
-  const float r = __fmul_rn((float)plan_uniform((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi), Wt);
-  float cacc = 0.f, cprev = 0.f, ck = 0.f;
-  int found = -1, lastnz = CENTER;
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    if (w[k] > 0.f) {
-      const float cn = cacc + w[k];
-      if (found < 0 && r < cn) {
-        found = k;
-        cprev = cacc;
-        ck = cn;
-      }
-      lastnz = k;
-      cacc = cn;
-    }
-  }
-  if (DIAG) {
-    float* dp = a.diag_p32 + (a.diag_base[rep] + slot) * (int64_t)kMaxK;
-    float cc = 0.f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      cc = (w[k] > 0.f) ? cc + w[k] : cc;
-      dp[k] = cc / Wt;
-    }
-  }
-  bool ok;
-  int kk;
-  if (found >= 0) {
-    kk = found;
-    const float mw = R.margin * Wt;
-    ok = (r > cprev + mw) && (r < ck - mw);
-  } else {
-    kk = lastnz;
-    ok = false;
-  }
-  int dxk = 0, dyk = 0;
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-    if (k == kk) {
-      dxk = T.dx[k];
-      dyk = T.dy[k];
-    }
-  const int target = cell + dyk * R.W + dxk;
-  if (DIAG) {
-    const int64_t di = a.diag_base[rep] + slot;
-    a.diag_choice32[di] = target;
-    a.diag_flag[di] = ok ? 0 : 1;
-  }
-  if (ok || norecheck) {
-    R.desired[slot] = target;
-    set_static(R.rec, cell, rec0, target == cell);
-  } else {
-    const uint32_t qi = append_slot(&a.ctl->q_count);
-    if (qi < a.q_cap) a.queue[qi] = ((uint32_t)rep << 24) | (uint32_t)slot;
-  }
+  const float u = (float)plan_uniform((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
+  finish_g1<K, CENTER, DIAG>(a, R, rep, slot, cell, Wt, u, norecheck, s_dxdy,
+                             [&](int k) { return w[k]; });
 }
 
 template <int V, int REACH, bool DIAG>
 __global__ void __launch_bounds__(256, 2) k_plan_tile(StepArgs a, Chunks ch, int norecheck) {
   extern __shared__ __align__(16) uint32_t s_tiles[];
+  __shared__ int s_dxdy[reach_count(V, REACH)];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t* tile = s_tiles + warp * (kTileH * kTileP);
   const int t = a.ctl->t;
+  fill_dxdy<V, REACH>(s_dxdy);
+  __syncthreads();
   for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
     const int rep = ch.rep[c];
     const RepDev& R = a.reps[rep];
@@ -374,11 +391,12 @@ __global__ void __launch_bounds__(256, 2) k_plan_tile(StepArgs a, Chunks ch, int
       if (live)
         plan_one_g1<V, REACH, DIAG, true>(a, R, rep, slot, cell,
                                           tile + (y - by0) * kTileP + (x - bx0), kTileP, t,
-                                          norecheck);
+                                          norecheck, s_dxdy);
     } else {
       if (lane == 0) atomicAdd(&a.ctl->tile_fallbacks, 1ull);
       if (live)
-        plan_one_g1<V, REACH, DIAG, false>(a, R, rep, slot, cell, R.rec + cell, W, t, norecheck);
+        plan_one_g1<V, REACH, DIAG, false>(a, R, rep, slot, cell, R.rec + cell, W, t, norecheck,
+                                           s_dxdy);
     }
     __syncwarp();
   }
