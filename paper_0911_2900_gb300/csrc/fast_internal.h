@@ -61,8 +61,8 @@ struct Ctl {
   uint32_t q_count;           // FP64 re-check queue length, this step
   uint32_t act_count[3];      // [2]: movers this step
   uint32_t wait_count[3];     // movers still waiting after each round (rotation)
-  uint32_t bar_count;         // grid barrier arrivals
-  uint32_t bar_gen;           // grid barrier generation
+  uint32_t bar_count;         // grid barrier arrivals of the running cooperative launch
+  uint32_t pad_bar;
   int32_t rounds_last;        // movement rounds of the last step
   int32_t rounds_max;
   int32_t resort_period;      // re-sort agents every this many steps (0: never)

@@ -194,37 +194,34 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
 }
 
 // ---------------------------------------------------------------------------
-// Grid-wide barrier for a cooperative launch, with a time limit: a block that
-// waits longer than ctl->barrier_ns_limit records the timeout in ctl->err and
-// every block then leaves the kernel at its next barrier.
-__device__ bool grid_barrier(Ctl* ctl) {
+// Grid-wide barrier for a cooperative launch, with a time limit.  The
+// arrival counter only grows during a launch (it is zero when the launch
+// starts): the n-th barrier of a block completes once n * gridDim.x blocks
+// have arrived.  A block that waits longer than ctl->barrier_ns_limit records
+// the timeout in ctl->err, and every block then leaves the kernel at its next
+// barrier.  `passed` counts the barriers this block has completed.
+__device__ bool grid_barrier(Ctl* ctl, uint32_t& passed) {
   __shared__ int s_ok;
   __syncthreads();
+  ++passed;
   if (threadIdx.x == 0) {
-    volatile uint32_t* vgen = &ctl->bar_gen;
+    volatile uint32_t* vcount = &ctl->bar_count;
     volatile int* verr = &ctl->err;
-    const uint32_t g = *vgen;
+    const uint32_t target = passed * gridDim.x;
     __threadfence();
-    const uint32_t arrived = atomicAdd(&ctl->bar_count, 1u);
+    atomicAdd(&ctl->bar_count, 1u);
     int ok = 1;
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&ctl->bar_gen, 1u);
-    } else {
-      const unsigned long long t0 = global_ns();
-      const unsigned long long lim = ctl->barrier_ns_limit;
-      while (*vgen == g) {
-        if (*verr != 0) {
-          ok = 0;
-          break;
-        }
-        if (global_ns() - t0 > lim) {
-          atomicCAS(&ctl->err, 0, kDevErrTimeout);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    const unsigned long long t0 = global_ns();
+    const unsigned long long lim = ctl->barrier_ns_limit;
+    while (*vcount < target) {
+      if (*verr != 0) {
+        ok = 0;
+        break;
+      }
+      if (global_ns() - t0 > lim) {
+        atomicCAS(&ctl->err, 0, kDevErrTimeout);
+        ok = 0;
+        break;
       }
     }
     __threadfence();
@@ -235,13 +232,13 @@ __device__ bool grid_barrier(Ctl* ctl) {
   return s_ok != 0;
 }
 
-__device__ __forceinline__ bool round_barrier(Ctl* ctl, bool single) {
+__device__ __forceinline__ bool round_barrier(Ctl* ctl, bool single, uint32_t& passed) {
   if (single) {
     __threadfence_block();
     __syncthreads();
     return true;
   }
-  return grid_barrier(ctl);
+  return grid_barrier(ctl, passed);
 }
 
 // Footprint of a mover at (x0, y0): row-major cells c[s] (records) and the
@@ -369,6 +366,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   __shared__ uint32_t s_base;
   build_path_tab(&tab);
   Ctl* ctl = a.ctl;
+  uint32_t nbar = 0;                     // grid barriers passed
   uint32_t g = __ldcg(&ctl->claim_tag);  // tag of the current round
   const uint32_t n0 = min(__ldcg(&ctl->act_count[2]), a.act_cap);
   const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
@@ -404,7 +402,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
       if (s <= n) atomicMin(&cl[q[s]], v);
   }
   if (tid == 0) atomicMax(&ctl->phase_ns[3], global_ns() - t_start);
-  if (!grid_barrier(ctl)) return;
+  if (!grid_barrier(ctl, nbar)) return;
 
   // ---- round 0: the ones that must wait claim for round 1 and go to the
   // block's global staging area
@@ -460,7 +458,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
     atomicMax(&ctl->phase_ns[4], (unsigned long long)nb);
     atomicMax(&ctl->phase_ns[5], (unsigned long long)w0);
   }
-  if (!grid_barrier(ctl)) return;
+  if (!grid_barrier(ctl, nbar)) return;
   if (tid == 0) atomicMax(&ctl->phase_ns[1], global_ns() - t_start);
   uint32_t waiting = __ldcg(&ctl->wait_count[1]);
   if (b == 0 && tid == 0) {
@@ -476,10 +474,10 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
       // with the first tag
       __syncthreads();
       clear_all_claims(a, single);
-      if (!round_barrier(ctl, single)) return;
+      if (!round_barrier(ctl, single, nbar)) return;
       g = 0u;
       claim_list(a, &tab, ml, ml.list(in_l), s_cnt[in_l], 0u);
-      if (!round_barrier(ctl, single)) return;
+      if (!round_barrier(ctl, single, nbar)) return;
     } else {
       ++g;
     }
@@ -498,7 +496,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
         e.info = ml.IN[idx];
         a.act[0][s_base + k] = e;
       }
-      if (!grid_barrier(ctl)) return;
+      if (!grid_barrier(ctl, nbar)) return;
       if (b != 0) return;
       const uint32_t nt = __ldcg(&ctl->tail_count);
       ml = smem_lists(dsm);
@@ -571,7 +569,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
       waiting = s_cnt[out_l];
     } else {
       if (tid == 0 && s_cnt[out_l]) atomicAdd(&ctl->wait_count[(r + 1) % 3], s_cnt[out_l]);
-      if (!grid_barrier(ctl)) return;
+      if (!grid_barrier(ctl, nbar)) return;
       waiting = __ldcg(&ctl->wait_count[(r + 1) % 3]);
     }
     if (b == 0 && tid == 0 && r < kRoundLog) {
@@ -597,9 +595,10 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
 // Cost of the grid barrier: `iters` barriers in a row, block 0 thread 0
 // records the elapsed global time in ctl->round_ns[0].
 __global__ void __launch_bounds__(1024, 1) k_barrier_cost(Ctl* ctl, int iters) {
+  uint32_t nbar = 0;
   const unsigned long long t0 = global_ns();
   for (int i = 0; i < iters; ++i)
-    if (!grid_barrier(ctl)) return;
+    if (!grid_barrier(ctl, nbar)) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->round_ns[0] = global_ns() - t0;
 }
 
@@ -624,6 +623,7 @@ __device__ __forceinline__ void reset_step_counters(Ctl* c) {
     c->wait_count[i] = 0u;
   }
   c->tail_count = 0u;
+  c->bar_count = 0u;
 }
 
 __global__ void k_step_begin(StepArgs a) {
@@ -692,7 +692,8 @@ int step_end_launch(const StepArgs& a, cudaStream_t s) {
 // report the timeout in ctl->err.
 __global__ void k_test_barrier_timeout(Ctl* ctl) {
   if (blockIdx.x == 0) return;
-  grid_barrier(ctl);
+  uint32_t nbar = 0;
+  grid_barrier(ctl, nbar);
 }
 
 int test_barrier_timeout_launch(Ctl* ctl, int grid, cudaStream_t s) {

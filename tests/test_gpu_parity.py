@@ -366,3 +366,27 @@ def test_precision_form_full_size_one_step(fg, orc):
     want_des[alive] = r["desired"]
     assert np.array_equal(des[cells >= 0], want_des[cells >= 0])
     assert np.array_equal(cells, sim.cells_by_id())
+
+
+def test_stress_form_full_size_one_step(fg, orc):
+    """16384x16384, 10M uniform agents, v_m=5, FP32 + FP64 re-check with the
+    spatial re-sort every 8 steps: after 7 steps, step 7 (which re-sorts at
+    its end) gives the oracle's desired cells and positions for every agent
+    when the oracle starts from the GPU's state; the FP32-only draw flips
+    only inside the margin."""
+    w = wl.config_stress()
+    ctx, (g7,) = run_gpu(fg, [w], 7, "fp32_recheck", digests=False)
+    rep = ctx.precision_report()
+    assert rep["flips_unflagged"] == 0
+    assert rep["flagged"] < 0.02 * rep["agents"]
+    alive = np.flatnonzero(g7["cells"] >= 0).astype(np.int32)
+    sim = orc.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed)
+    sim.place(g7["cells"][alive], ids=alive)
+    ctx.step(1)
+    cells, des, st = ctx.readback(0, len(w.cells))
+    r = sim.run(7, 1, threads=os.cpu_count() or 1, digests=False)
+    want_des = np.full(len(w.cells), -1, np.int32)
+    want_des[alive] = r["desired"]
+    assert np.array_equal(des[cells >= 0], want_des[cells >= 0])
+    assert np.array_equal(cells, sim.cells_by_id())
+    assert st["alive"] + st["exited"] == len(w.cells)
