@@ -92,6 +92,11 @@ def parse():
     p.add_argument("--workload", default="precision",
                    choices=["precision", "room", "corridors", "stress", "batch"])
     p.add_argument("--no-tune", action="store_true")
+    p.add_argument("--tune-cache", default=None,
+                   help="JSON file: reuse the autotuner's choice for this workload and GPU "
+                        "if stored there, else tune and store it")
+    p.add_argument("--v-m", type=int, default=None,
+                   help="v_m of the room and corridors workloads (default 4)")
     p.add_argument("--fp64-steps", type=int, default=3)
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-steps", type=int, default=2)
@@ -107,16 +112,16 @@ def dist_env():
     return rank, world, local
 
 
-def make_workloads(name, rank):
+def make_workloads(name, rank, v_m=None):
     """The replicates one rank simulates (one context)."""
     from paper_0911_2900_gb300 import workloads as wl
 
     if name == "precision":
         return [wl.config_precision(seed=rank)]
     if name == "room":
-        return [wl.config_small_room(seed=rank)]
+        return [wl.config_small_room(seed=rank, v_m=v_m or 4)]
     if name == "corridors":
-        return [wl.config_corridors(v_m=4, seed=rank)]
+        return [wl.config_corridors(v_m=v_m or 4, seed=rank)]
     if name == "batch":
         return wl.config_batch(seed=rank)
     return [wl.config_stress(seed=rank)]
@@ -272,7 +277,7 @@ def bench_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    works = make_workloads(args.workload, 0)
+    works = make_workloads(args.workload, 0, args.v_m)
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
     c = cpu_oracle_rate(works, args.steps, threads, warmup=args.warmup)
@@ -317,7 +322,7 @@ def bench_ours(args):
 
             dist.barrier()
 
-    works = make_workloads(args.workload, rank)
+    works = make_workloads(args.workload, rank, args.v_m)
     label = workload_label(works)
     n_rep = len(works)
     n0 = [int(len(w.cells)) for w in works]
@@ -368,7 +373,9 @@ def bench_ours(args):
 
     # ---- FP32 + FP64 re-check -------------------------------------------------
     ctx = make_ctx("fp32_recheck")
-    tune = ctx.autotune(trials=3) if not args.no_tune else None
+    tune = None
+    if not args.no_tune:
+        tune = ctx.autotune(trials=3, cache=args.tune_cache, key=label)
     if loop_graph:
         # warm-up steps, then capture the timed loop's graph with an untimed
         # run of the same length at the same step phase (period 8)
@@ -432,6 +439,10 @@ def bench_ours(args):
     achieved = bytes_plan / (statistics.mean(plan_ms) / 1e3) / 1e9
     bytes_move = move_bytes(movers, foot)
     achieved_move = bytes_move / (statistics.mean(rounds_ms) / 1e3) / 1e9
+
+    # FP32 draws against the FP64 rule on the current state (not timed):
+    # flips before the re-check, and that none falls outside the margin
+    prec = ctx.precision_report()
 
     # the planning kernel the tuned context runs for v_m = 4 (or its only v_m)
     v_main = 4 if any(w.v_m == 4 for w in works) else works[0].v_m
@@ -533,6 +544,8 @@ def bench_ours(args):
                          "move_prep": statistics.mean(prep_ms),
                          "move_rounds": statistics.mean(rounds_ms),
                          "other": statistics.mean(other_ms)},
+            "precision_report": {k: (float(v) if isinstance(v, float) else int(v))
+                                 for k, v in prec.items()},
             "movers_per_step": movers,
             "rechecked_per_step": rechecked,
             "tile_fallback_warps_per_step": fallbacks,
