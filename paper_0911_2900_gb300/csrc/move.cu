@@ -39,6 +39,8 @@ constexpr int MV_DX = 4;               // dx + 8, 4 bits
 constexpr int MV_DY = 8;               // dy + 8, 4 bits
 constexpr int MV_FIN = 13;             // first-round outcome: last path step entered (3 bits)
 constexpr uint32_t MV_GONE = 1u << 16; // first-round outcome: leaves through an exit
+constexpr int MV_NEED = 17;            // footprint cells (bit s: cell s) whose claim the
+                                       // agent has not held yet (6 bits)
 
 constexpr int kTail = 1024;            // waiting movers one block finishes alone
 
@@ -418,10 +420,10 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
     uint32_t cl[6];
 #pragma unroll
     for (int s = 0; s < 6; ++s) cl[s] = (s <= n) ? __ldcg(&now[q[s]]) : mine_v;
-    bool mine = true;
+    uint32_t need = 0u;
 #pragma unroll
-    for (int s = 0; s < 6; ++s) mine &= (cl[s] == mine_v);
-    if (mine) {
+    for (int s = 0; s < 6; ++s) need |= (cl[s] != mine_v) ? (1u << s) : 0u;
+    if (need == 0u) {
       commit_first(a, R, rep, slot, c, e.info);
     } else {
       if (reclaim) {
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
       gl.P[j] = e.prio;
       gl.C0[j] = e.c0;
       gl.RF[j] = e.ref;
-      gl.IN[j] = e.info;
+      gl.IN[j] = (e.info & ~(0x3Fu << MV_NEED)) | (need << MV_NEED);
     }
   }
   __syncthreads();
@@ -539,12 +541,16 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
       const int n = (int)(info & MV_LEN);
       const uint32_t* now = R.claim[g & 1u];
       const uint32_t mine_v = claim_of(g, p);
+      // only the cells not held yet need a look: a cell once held stays
+      // held, since its claimants can only leave
+      const uint32_t need0 = (info >> MV_NEED) & 0x3Fu;
       uint32_t cl[6];
 #pragma unroll
-      for (int s = 0; s < 6; ++s) cl[s] = (s <= n) ? __ldcg(&now[q[s]]) : mine_v;
-      bool mine = true;
+      for (int s = 0; s < 6; ++s) cl[s] = ((need0 >> s) & 1u) ? __ldcg(&now[q[s]]) : mine_v;
+      uint32_t need = 0u;
 #pragma unroll
-      for (int s = 0; s < 6; ++s) mine &= (cl[s] == mine_v);
+      for (int s = 0; s < 6; ++s) need |= (cl[s] != mine_v) ? (1u << s) : 0u;
+      const bool mine = need == 0u;
       if (mine) {
         const int wl = walk_len(info);
         uint32_t pr[6];
@@ -559,6 +565,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
           for (int s = 0; s < 6; ++s)
             if (s <= n) atomicMin(&nxt[q[s]], v);
         }
+        if (need != need0) ml.IN[idx] = (info & ~(0x3Fu << MV_NEED)) | (need << MV_NEED);
         lout[append_slot(&s_cnt[out_l])] = idx;
       }
     }
