@@ -13,8 +13,9 @@ movement phase, emulated in rounds -- over the precision workload: a
   choices_per_s  desired-cell choices/s of the planning phase alone
   fp64_form    the same with every agent planned by the all-FP64 kernel
   e2e          agent-steps/s through the public API with host buffers: each
-               step places the state from pinned host memory, steps once and
-               reads cells and desired cells back
+               step places every replicate's cells-by-id array from pinned
+               host memory (as the previous step read it back; -1 = left),
+               steps once and reads cells and desired cells back into it
   roofline     the dominant kernel (movement rounds): algorithmic bytes per
                launch / its average event time, against the measured HBM copy
                bandwidth; roofline_plan the same for the planning kernel
@@ -463,21 +464,19 @@ def bench_ours(args):
     ctx64.close()
 
     # ---- end to end through the public API with host buffers ---------------------
-    hc, hi, oc, od = [], [], [], []
+    # each step: place every replicate from its pinned cells-by-id array (-1:
+    # left), step once, read cells and desired cells back into the same arrays
+    oc, od, live = [], [], []
     t_step = None
     for r in range(n_rep):
-        cells_d, _, st = ctx.readback(r, n0[r])
+        a = torch.empty(n0[r], dtype=torch.int32, pin_memory=True).numpy()
+        b = torch.empty(n0[r], dtype=torch.int32, pin_memory=True).numpy()
+        _, _, st = ctx.readback(r, n0[r], cells_out=a, desired_out=b)
         t_step = st["step"]
-        ids = np.flatnonzero(cells_d >= 0).astype(np.int32)
-        a = torch.empty(len(ids), dtype=torch.int32, pin_memory=True).numpy()
-        b = torch.empty(len(ids), dtype=torch.int32, pin_memory=True).numpy()
-        a[:] = cells_d[ids]
-        b[:] = ids
-        hc.append(a)
-        hi.append(b)
-        oc.append(torch.empty(n0[r], dtype=torch.int32, pin_memory=True).numpy())
-        od.append(torch.empty(n0[r], dtype=torch.int32, pin_memory=True).numpy())
-    h2d = 8 * sum(len(a) for a in hc)
+        oc.append(a)
+        od.append(b)
+        live.append(st["alive"])
+    h2d = 4 * sum(n0)
     d2h = 8 * sum(n0)
     e2e_agent_steps = 0
     barrier()
@@ -485,18 +484,11 @@ def bench_ours(args):
     t_e2e = time.perf_counter()
     for i in range(args.e2e_steps):
         for r in range(n_rep):
-            ctx.place(r, hc[r], ids=hi[r], start_step=t_step)
+            ctx.place(r, oc[r], start_step=t_step)
         ctx.step(1)
+        e2e_agent_steps += sum(live)
         for r in range(n_rep):
-            ctx.readback(r, n0[r], cells_out=oc[r], desired_out=od[r])
-            e2e_agent_steps += len(hc[r])
-            keep = oc[r][hi[r]] >= 0
-            ids_new = hi[r][keep]
-            cells_new = oc[r][ids_new]
-            hc[r] = hc[r][:len(ids_new)]
-            hi[r] = hi[r][:len(ids_new)]
-            hc[r][:] = cells_new
-            hi[r][:] = ids_new
+            live[r] = ctx.readback(r, n0[r], cells_out=oc[r], desired_out=od[r])[2]["alive"]
         t_step += 1
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t_e2e

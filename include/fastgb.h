@@ -159,10 +159,15 @@ int fast_init_grid(fast_ctx* ctx, int32_t replicate, const fast_grid_desc* grid)
 
 /* Places n agents of one replicate (replacing any previous ones).
  * cells: host [n] distinct free, reachable, non-exit cells (NULL: error);
- * ids: host [n] distinct ids in [0, 2^24) (NULL: 0..n-1);
+ * ids: host [n] distinct ids in [0, 2^24); NULL: agent i has id i, and
+ * cells[i] == -1 means there is no agent with id i (so the cells-by-id array
+ * that fast_readback writes can be placed again as it is);
  * start_step: index of the next step (all replicates share one step index;
  * resuming a run = placing its read-back state with its step index).
- * Errors: FAST_EINVAL, FAST_ESTATE (grid not set), FAST_ENOMEM, FAST_ECUDA. */
+ * The cells and ids are checked on the device.  Errors: FAST_EINVAL (a cell
+ * outside the grid, on a wall, unreachable, an exit or taken twice, or an id
+ * out of range or repeated; the replicate is then left without agents),
+ * FAST_ESTATE (grid not set), FAST_ENOMEM, FAST_ECUDA. */
 int fast_place_agents(fast_ctx* ctx, int32_t replicate, int32_t n, const int32_t* cells,
                       const int32_t* ids, int32_t start_step);
 

@@ -6,6 +6,7 @@
 // move.cu and aux.cu; the host only computes the exact floor field at grid
 // set-up (floor_field.cpp) and checks placements.
 #include <algorithm>
+#include <climits>
 #include <cstddef>
 #include <cmath>
 #include <cstdarg>
@@ -42,11 +43,8 @@ struct RepHost {
   int32_t W = 0, H = 0, v = 0, K = 0, mw = 1;
   double kS = 0.0;
   uint64_t seed = 0;
-  std::vector<uint8_t> placeable;  // free and reachable
-  std::vector<uint8_t> seen;       // duplicate check scratch
   int32_t cap = 0;                 // agent slots allocated
   int32_t n = 0;                   // agents placed
-  int32_t id_bound = 0;            // max id + 1
   RepDev d{};                      // device pointers and parameters
 };
 
@@ -85,6 +83,8 @@ struct fast_ctx {
   int32_t dig_cap = 0;
   int32_t* d_gather = nullptr;
   int32_t gather_cap = 0;
+  uint32_t* d_id_bits = nullptr;  // 2^24-bit set of the ids a placement has seen
+  int32_t* d_place_err = nullptr;  // placement check: first bad index, agents placed
 
   struct Group {
     int v = 0;
@@ -631,8 +631,6 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   exact_floor_field(g->width, g->height, g->cell_type, a.data(), b.data());
   std::vector<uint32_t> rec(C);
   RepHost& R = c->reps[r];
-  R.placeable.assign(C, 0);
-  R.seen.assign(C, 0);
   for (int64_t i = 0; i < C; ++i) {
     if (a[i] < 0) {
       rec[i] = 0x7FFFu | (0x7FFFu << 15) | 0x40000000u;
@@ -641,7 +639,6 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
     if (a[i] > 0x7FFE || b[i] > 0x7FFE)
       return fail(c, FAST_EINVAL, "distance to the nearest exit too long at cell %lld", (long long)i);
     rec[i] = (uint32_t)a[i] | ((uint32_t)b[i] << 15);
-    R.placeable[i] = g->cell_type[i] == FAST_CELL_FREE;
   }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   // (re)allocate the per-cell arrays
@@ -697,45 +694,10 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
   if (!rep_ok(c, r)) return fail(c, FAST_EINVAL, "bad replicate index %d", r);
   RepHost& R = c->reps[r];
   if (!R.grid_set) return fail(c, FAST_ESTATE, "grid of replicate %d not set", r);
-  if (n < 0 || n >= (1 << kMaxIdBits)) return fail(c, FAST_EINVAL, "agent count %d out of range", n);
+  if (n < 0 || n > (1 << kMaxIdBits)) return fail(c, FAST_EINVAL, "agent count %d out of range", n);
   if (n > 0 && !cells) return fail(c, FAST_EINVAL, "cells is NULL");
   if (start_step < 0) return fail(c, FAST_EINVAL, "start_step < 0");
   const int64_t C = (int64_t)R.W * R.H;
-  // validate cells: placeable and distinct
-  int32_t bad = -1;
-  for (int32_t i = 0; i < n; ++i) {
-    const int32_t cc = cells[i];
-    if (cc < 0 || cc >= C || !R.placeable[cc] || R.seen[cc]) {
-      bad = i;
-      break;
-    }
-    R.seen[cc] = 1;
-  }
-  for (int32_t i = 0; i < n && (bad < 0 || i < bad); ++i) R.seen[cells[i]] = 0;
-  if (bad >= 0)
-    return fail(c, FAST_EINVAL, "agent %d: cell %d is outside, not free, unreachable, an exit or taken",
-                bad, cells[bad]);
-  int32_t id_bound = n;
-  std::vector<int32_t> gen_ids;
-  if (ids) {
-    std::vector<uint8_t> seen_id;
-    int32_t mx = -1;
-    for (int32_t i = 0; i < n; ++i) {
-      if (ids[i] < 0 || ids[i] >= (1 << kMaxIdBits))
-        return fail(c, FAST_EINVAL, "agent %d: id %d not in [0, 2^24)", i, ids[i]);
-      mx = std::max(mx, ids[i]);
-    }
-    seen_id.assign((size_t)mx + 1, 0);
-    for (int32_t i = 0; i < n; ++i) {
-      if (seen_id[ids[i]]) return fail(c, FAST_EINVAL, "duplicate id %d", ids[i]);
-      seen_id[ids[i]] = 1;
-    }
-    id_bound = mx + 1;
-  } else {
-    gen_ids.resize(n);
-    for (int32_t i = 0; i < n; ++i) gen_ids[i] = i;
-    ids = gen_ids.data();
-  }
 
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   // clear the previous agents' occupancy marks
@@ -758,20 +720,51 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
     R.d.cap = cap;
     c->layout_dirty = true;
   }
+  if (ids && !c->d_id_bits) {
+    if (int e = alloc_into(c, &c->d_id_bits, (size_t)1 << (kMaxIdBits - 5))) return e;
+    CUDA_TRY(c, cudaMemsetAsync(c->d_id_bits, 0, (size_t)4 << (kMaxIdBits - 5), c->stream));
+  }
+  if (!c->d_place_err)
+    if (int e = alloc_into(c, &c->d_place_err, 2)) return e;
   R.placed = true;
-  R.n = n;
-  R.id_bound = id_bound;
+  R.n = 0;
   CUDA_TRY(c, cudaMemsetAsync(R.d.cell, 0xFF, (size_t)R.cap * 4, c->stream));
+  const int32_t init[2] = {INT32_MAX, 0};
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_place_err, init, 8, cudaMemcpyHostToDevice, c->stream));
   if (n > 0) {
     CUDA_TRY(c, cudaMemcpyAsync(R.d.cell2, cells, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
-    CUDA_TRY(c, cudaMemcpyAsync(R.d.id2, ids, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
+    if (ids)
+      CUDA_TRY(c, cudaMemcpyAsync(R.d.id2, ids, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
   }
   if (c->layout_dirty) {
     if (int e = rebuild_layout(c)) return e;
   }
-  LAUNCH_TRY(c, place_launch(c->d_reps + r, R.d.cell2, R.d.id2, n, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots + r, &n, 4, cudaMemcpyHostToDevice, c->stream));
+  // the check and the placement in one pass on the device (slots 0..n-1)
+  uint8_t* placed = reinterpret_cast<uint8_t*>(R.d.mvinfo);
+  LAUNCH_TRY(c, place_checked_launch(c->d_reps + r, R.d.cell2, ids ? R.d.id2 : nullptr, n, C,
+                                     c->d_id_bits, placed, c->d_place_err, c->stream));
+  int32_t res[2] = {INT32_MAX, 0};
+  CUDA_TRY(c, cudaMemcpyAsync(res, c->d_place_err, 8, cudaMemcpyDeviceToHost, c->stream));
+  if (ids)
+    CUDA_TRY(c, cudaMemsetAsync(c->d_id_bits, 0, (size_t)4 << (kMaxIdBits - 5), c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   const int32_t zero = 0;
+  if (res[0] != INT32_MAX) {
+    // undo: the replicate is left without agents
+    LAUNCH_TRY(c, place_rollback_launch(c->d_reps + r, R.d.cell2, n, placed, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots + r, &zero, 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_exited + r, &zero, 4, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int32_t bad_cell = -1, bad_id = res[0];
+    if (cells) bad_cell = cells[res[0]];
+    if (ids) bad_id = ids[res[0]];
+    return fail(c, FAST_EINVAL,
+                "agent %d (id %d): cell %d is outside, not free, unreachable, an exit or taken, "
+                "or the id is outside [0, 2^24) or repeated; the replicate now has no agents",
+                res[0], bad_id, bad_cell);
+  }
+  R.n = res[1];
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots + r, &n, 4, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(c->d_exited + r, &zero, 4, cudaMemcpyHostToDevice, c->stream));
   // step index and per-step counters
   CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->t, &start_step, 4, cudaMemcpyHostToDevice, c->stream));

@@ -61,20 +61,75 @@ int clear_occ_launch(RepDev* d, const int32_t* n_slots, int rep, int cap, cudaSt
   return 0;
 }
 
-__global__ void k_place(RepDev* rp, const int32_t* cells, const int32_t* ids, int n) {
+// Places agents i < n in slots i, checking on the device what the host used
+// to check: the cell is inside the grid, free, reachable and not an exit, no
+// two agents share a cell, and (with explicit ids) every id is in [0, 2^24)
+// and unique.  The occupancy bit is taken with an atomic, so a taken cell is
+// found by whichever agent comes second.  Without explicit ids, id i is
+// absent when cells[i] == -1.  err[0] receives the smallest failing index,
+// err[1] the number of agents placed; placed[i] marks the cells this call
+// took, for a roll-back.
+__global__ void k_place_checked(RepDev* rp, const int32_t* cells, const int32_t* ids, int n,
+                                long long n_cells, uint32_t* id_bits, uint8_t* placed,
+                                int32_t* err) {
   const RepDev& R = *rp;
+  int present = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int c = cells[i];
-    R.cell[i] = c;
-    R.id[i] = ids[i];
-    R.desired[i] = c;
-    R.rec[c] = (R.rec[c] & ~REC_STA) | REC_OCC;
+    const int id = ids ? ids[i] : i;
+    placed[i] = 0;
+    if (!ids && c == -1) {
+      R.cell[i] = -1;
+      R.id[i] = i;
+      R.desired[i] = -1;
+      continue;
+    }
+    bool ok = c >= 0 && (long long)c < n_cells;
+    if (ok) {
+      const uint32_t old = atomicOr(&R.rec[c], REC_OCC);
+      if (!(old & REC_OCC)) placed[i] = 1;
+      ok = !(old & REC_OCC) && !rec_exit(old);
+    }
+    if (ok && ids) {
+      ok = id >= 0 && id < (1 << kMaxIdBits);
+      if (ok) {
+        const uint32_t bit = 1u << (id & 31);
+        ok = !(atomicOr(&id_bits[id >> 5], bit) & bit);
+      }
+    }
+    if (!ok) atomicMin(&err[0], i);
+    R.cell[i] = ok ? c : -1;
+    R.id[i] = id;
+    R.desired[i] = ok ? c : -1;
+    ++present;
+  }
+  for (int o = 16; o > 0; o >>= 1) present += __shfl_xor_sync(0xffffffffu, present, o);
+  if ((threadIdx.x & 31) == 0 && present) atomicAdd(&err[1], present);
+}
+
+// Undoes the occupancy bits a failed placement took.
+__global__ void k_place_rollback(RepDev* rp, const int32_t* cells, int n, const uint8_t* placed) {
+  const RepDev& R = *rp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (placed[i]) atomicAnd(&R.rec[cells[i]], ~(REC_OCC | REC_STA));
+    R.cell[i] = -1;
   }
 }
 
-int place_launch(RepDev* d, const int32_t* cells, const int32_t* ids, int n, cudaStream_t s) {
+int place_checked_launch(RepDev* d, const int32_t* cells, const int32_t* ids, int n,
+                         long long n_cells, uint32_t* id_bits, uint8_t* placed, int32_t* err,
+                         cudaStream_t s) {
   if (n <= 0) return 0;
-  k_place<<<(n + 255) / 256, 256, 0, s>>>(d, cells, ids, n);
+  const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  k_place_checked<<<grid, 256, 0, s>>>(d, cells, ids, n, n_cells, id_bits, placed, err);
+  return 0;
+}
+
+int place_rollback_launch(RepDev* d, const int32_t* cells, int n, const uint8_t* placed,
+                          cudaStream_t s) {
+  if (n <= 0) return 0;
+  const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  k_place_rollback<<<grid, 256, 0, s>>>(d, cells, n, placed);
   return 0;
 }
 

@@ -139,8 +139,11 @@ int resort_launch(const StepArgs& a, const Chunks& ch, int grid, bool force, cud
 int masks_launch(const RepDev& host_rep, RepDev* dev_rep, int64_t cells, cudaStream_t s);
 int clear_occ_launch(RepDev* dev_rep, const int32_t* n_slots_dev, int rep, int cap,
                      cudaStream_t s);
-int place_launch(RepDev* dev_rep, const int32_t* cells, const int32_t* ids, int n,
-                 cudaStream_t s);
+int place_checked_launch(RepDev* dev_rep, const int32_t* cells, const int32_t* ids, int n,
+                         long long n_cells, uint32_t* id_bits, uint8_t* placed, int32_t* err,
+                         cudaStream_t s);
+int place_rollback_launch(RepDev* dev_rep, const int32_t* cells, int n, const uint8_t* placed,
+                          cudaStream_t s);
 int gather_by_id_launch(const RepDev* dev_rep, const int32_t* n_slots_dev, int rep, int cap,
                         int32_t* out_cell, int32_t* out_desired, int32_t bound,
                         cudaStream_t s);

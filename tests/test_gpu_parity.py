@@ -259,6 +259,14 @@ def test_resume_is_bit_exact(fg, orc):
     ctx2.step(10)
     cells, _, st = ctx2.readback(0, len(w.cells))
     assert np.array_equal(cells, g20["cells"])
+    # the cells-by-id array as read back (-1: left) placed again as it is
+    ctx3 = fg.Context(1, "fp32_recheck")
+    ctx3.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx3.place(0, g10["cells"], start_step=10)
+    ctx3.step(10)
+    cells3, _, st3 = ctx3.readback(0, len(w.cells))
+    assert np.array_equal(cells3, g20["cells"])
+    assert st3["alive"] == st["alive"]
 
 
 def test_edge_cases(fg, orc):
@@ -309,6 +317,8 @@ def test_invalid_inputs_are_rejected(fg):
         ctx.place(0, [25, 26], ids=[3, 3])     # duplicate ids
     with pytest.raises(fg.FastError):
         ctx.place(0, [25], ids=[1 << 24])      # id too large
+    _, _, st = ctx.readback(0, 0)
+    assert st["alive"] == 0                    # a rejected placement leaves no agents
     ctx.place(0, [25, 47])
     ctx.step(2)
     ctx.readback(0)
