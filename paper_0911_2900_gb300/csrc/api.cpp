@@ -645,6 +645,8 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   dfree(c, R.d.rec);
   dfree(c, R.d.mask);
   for (auto& p : R.d.claim) dfree(c, p);
+  dfree(c, R.d.cmark);
+  R.d.cmark = nullptr;
   R.d.rec = nullptr;
   R.d.mask = nullptr;
   R.d.claim[0] = R.d.claim[1] = nullptr;
@@ -660,6 +662,7 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   const int64_t claim_cells = (int64_t)((R.W + 15) / 16) * ((R.H + 15) / 16) * 256;
   for (auto& p : R.d.claim)
     if (int e = alloc_into(c, &p, claim_cells)) return e;
+  if (int e = alloc_into(c, &R.d.cmark, claim_cells)) return e;
   RepDev& d = R.d;
   d.W = R.W;
   d.H = R.H;
@@ -675,6 +678,7 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   CUDA_TRY(c, cudaMemcpyAsync(d.rec, rec.data(), C * 4, cudaMemcpyHostToDevice, c->stream));
   d.claim_tx = (R.W + 15) / 16;
   for (auto p : d.claim) CUDA_TRY(c, cudaMemsetAsync(p, 0xFF, claim_cells * 4, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(d.cmark, 0, claim_cells, c->stream));
   R.grid_set = true;
   R.placed = false;
   R.n = 0;
@@ -1262,6 +1266,7 @@ int fast_set_option(fast_ctx* c, int32_t option, int64_t value) {
         if (!R.grid_set) continue;
         const size_t n = (size_t)((R.W + 15) / 16) * ((R.H + 15) / 16) * 256;
         for (auto p : R.d.claim) CUDA_TRY(c, cudaMemsetAsync(p, 0xFF, n * 4, c->stream));
+        CUDA_TRY(c, cudaMemsetAsync(R.d.cmark, 0, n, c->stream));
       }
       if (int e = write_ctl_int(c, offsetof(Ctl, claim_tag), (int32_t)value)) return e;
       break;

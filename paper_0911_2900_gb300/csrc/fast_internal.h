@@ -45,6 +45,8 @@ struct RepDev {
   unsigned long long* mask;         // [W*H*mw] line-of-sight masks
   uint32_t* claim[2];               // movement claims: round tag << 24 | priority,
                                     // tile-major (16x16-cell tiles of 1 KB)
+  uint8_t* cmark;                   // same layout: stamp of the last step in which an
+                                    // agent lost the cell's first-round claim
   int32_t* id;                      // [cap]
   int32_t* cell;                    // [cap]  -1: slot empty / agent left
   int32_t* desired;                 // [cap]
@@ -71,6 +73,8 @@ struct Ctl {
   uint32_t tail_count;        // waiting movers handed to one block, this step
   uint32_t claim_tag;         // tag of the next step's first movement claims
   uint32_t tag_reserve;       // clear the claims before a step with fewer tags left
+  uint32_t mark_stamp;        // this step's stamp for contested-cell marks (1..254)
+  uint32_t pad3;
   unsigned long long rounds_total;
   unsigned long long rechecked_total;
   unsigned long long agent_steps;

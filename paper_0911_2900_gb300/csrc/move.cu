@@ -41,6 +41,9 @@ constexpr int MV_FIN = 13;             // first-round outcome: last path step en
 constexpr uint32_t MV_GONE = 1u << 16; // first-round outcome: leaves through an exit
 constexpr int MV_NEED = 17;            // footprint cells (bit s: cell s) whose claim the
                                        // agent has not held yet (6 bits)
+constexpr int MV_CLM = 23;             // footprint cells the agent must keep claiming in
+                                       // later rounds: those another agent also claims
+                                       // (6 bits)
 
 constexpr int kTail = 1024;            // waiting movers one block finishes alone
 
@@ -54,9 +57,10 @@ __device__ __forceinline__ uint32_t claim_of(uint32_t g, uint32_t prio) {
   return ((254u - g) << 24) | prio;
 }
 
-// Sets every claim of every replicate to "none": grid-stride, or by the
-// calling block alone.
-__device__ __forceinline__ void clear_all_claims(const StepArgs& a, bool block_only = false) {
+// Sets every claim of every replicate to "none" (and, with marks, every
+// contested-cell mark to "never"): grid-stride, or by the calling block alone.
+__device__ __forceinline__ void clear_all_claims(const StepArgs& a, bool block_only = false,
+                                                 bool marks = false) {
   const uint32_t stride = block_only ? blockDim.x : gridDim.x * blockDim.x;
   const uint32_t first = block_only ? threadIdx.x : blockIdx.x * blockDim.x + threadIdx.x;
   for (int r = 0; r < a.n_rep; ++r) {
@@ -67,18 +71,34 @@ __device__ __forceinline__ void clear_all_claims(const StepArgs& a, bool block_o
       __stcg(&R.claim[0][i], 0xFFFFFFFFu);
       __stcg(&R.claim[1][i], 0xFFFFFFFFu);
     }
+    if (marks)
+      for (uint32_t i = first; i < n / 4; i += stride)
+        __stcg(reinterpret_cast<uint32_t*>(R.cmark) + i, 0u);
   }
 }
 
-// Before the movement-order pass: clear the claims if this step could run
-// out of tags.
-__global__ void __launch_bounds__(256) k_claim_epoch(StepArgs a) {
-  if (__ldcg(&a.ctl->claim_tag) + a.ctl->tag_reserve <= kTags) return;
-  clear_all_claims(a);
+// A step starts a new claim epoch (all claims and marks cleared, tags and
+// mark stamps from the start) if it could run out of tags or stamps.
+__device__ __forceinline__ bool epoch_ends(const Ctl* ctl) {
+  return ctl->claim_tag + ctl->tag_reserve > kTags || ctl->mark_stamp >= 254u;
 }
 
+// Before the movement-order pass: clear the claims and marks at the end of
+// an epoch.
+__global__ void __launch_bounds__(256) k_claim_epoch(StepArgs a) {
+  if (!epoch_ends(a.ctl)) return;
+  clear_all_claims(a, false, true);
+}
+
+// Then the step's first tag and its mark stamp.
 __global__ void k_claim_epoch_done(StepArgs a) {
-  if (threadIdx.x == 0 && a.ctl->claim_tag + a.ctl->tag_reserve > kTags) a.ctl->claim_tag = 0u;
+  if (threadIdx.x != 0) return;
+  if (epoch_ends(a.ctl)) {
+    a.ctl->claim_tag = 0u;
+    a.ctl->mark_stamp = 1u;
+  } else {
+    a.ctl->mark_stamp += 1u;
+  }
 }
 
 // Place of cell (x, y) in the tile-major claim arrays (16x16-cell tiles).
@@ -370,6 +390,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   Ctl* ctl = a.ctl;
   uint32_t nbar = 0;                     // grid barriers passed
   uint32_t g = __ldcg(&ctl->claim_tag);  // tag of the current round
+  const uint8_t stamp = (uint8_t)__ldcg(&ctl->mark_stamp);
   const uint32_t n0 = min(__ldcg(&ctl->act_count[2]), a.act_cap);
   const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const uint32_t start = (uint32_t)(((unsigned long long)n0 * b) / G);
@@ -426,6 +447,10 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
     if (need == 0u) {
       commit_first(a, R, rep, slot, c, e.info);
     } else {
+      // the cells this agent lost are contested: mark them for this step
+#pragma unroll
+      for (int s = 0; s < 6; ++s)
+        if ((need >> s) & 1u) R.cmark[q[s]] = stamp;
       if (reclaim) {
         uint32_t* nxt = R.claim[(g + 1u) & 1u];
         const uint32_t v = claim_of(g + 1u, e.prio);
@@ -462,6 +487,23 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   }
   if (!grid_barrier(ctl, nbar)) return;
   if (tid == 0) atomicMax(&ctl->phase_ns[1], global_ns() - t_start);
+  // the cells each waiting agent must keep claiming: the ones it has not
+  // held, and the ones it held that another agent lost (claimed too); a
+  // cell only it claims is nobody else's concern for the rest of the step
+  for (uint32_t k = tid; k < w0; k += blockDim.x) {
+    const uint32_t info = ml.IN[k];
+    const RepDev& R = a.reps[ml.RF[k] >> 24];
+    int c[6], q[6];
+    foot_cells(&tab, ml.C0[k], R, info, c, q);
+    const int n = (int)(info & MV_LEN);
+    const uint32_t need = (info >> MV_NEED) & 0x3Fu;
+    uint32_t clm = need;
+#pragma unroll
+    for (int s = 0; s < 6; ++s)
+      if (s <= n && !((need >> s) & 1u) && __ldcg(&R.cmark[q[s]]) == stamp) clm |= 1u << s;
+    ml.IN[k] = (info & ~(0x3Fu << MV_CLM)) | (clm << MV_CLM);
+  }
+  __syncthreads();
   uint32_t waiting = __ldcg(&ctl->wait_count[1]);
   if (b == 0 && tid == 0) {
     ctl->round_n[0] = waiting;
@@ -561,9 +603,10 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
         if (reclaim) {
           uint32_t* nxt = R.claim[(g + 1u) & 1u];
           const uint32_t v = claim_of(g + 1u, p);
+          const uint32_t clm = (info >> MV_CLM) & 0x3Fu;
 #pragma unroll
           for (int s = 0; s < 6; ++s)
-            if (s <= n) atomicMin(&nxt[q[s]], v);
+            if ((clm >> s) & 1u) atomicMin(&nxt[q[s]], v);
         }
         if (need != need0) ml.IN[idx] = (info & ~(0x3Fu << MV_NEED)) | (need << MV_NEED);
         lout[append_slot(&s_cnt[out_l])] = idx;
