@@ -215,7 +215,8 @@ int reach_count_host(int v, int reach) {
 //   gamma = (1 + delta)(1 + 2^-24)^K - 1.
 // |C32/W32 - C*/W*| <= 2 gamma / (1 - gamma) for the FP32 side and 2A for the
 // FP64 side (A = 1e-10 bounds the FP64 rule's own error against exact
-// arithmetic); the test itself and u -> float add 2^-21.  M doubles the sum.
+// arithmetic); the test itself and the 24-bit float draw (|u - u24| < 2^-24)
+// add 2^-21.  M doubles the sum.
 float margin_of(int v, int K, double kS) {
   const double u24 = std::ldexp(1.0, -24);
   const double ds_err = std::ldexp(1.0, -23) * (v * kSqrt2 + 0.002);
@@ -419,7 +420,6 @@ int enqueue_step(fast_ctx* c, bool resort) {
   CUDA_TRY(c, record_event(c, 2));
   if (c->digests) LAUNCH_TRY(c, digest_des_launch(a, all, plan_grid(c, all.n), c->cur));
   LAUNCH_TRY(c, move_prep_launch(a, all, plan_grid(c, all.n), c->cur));
-  c->launches += 2;  // move_prep_launch queues three kernels
   CUDA_TRY(c, record_event(c, 3));
   LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), 1024, c->cur));
   CUDA_TRY(c, record_event(c, 4));

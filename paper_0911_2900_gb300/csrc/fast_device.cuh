@@ -102,6 +102,14 @@ __device__ __forceinline__ double plan_uniform(uint32_t id, uint32_t t, uint32_t
   return __dmul_rn(__dadd_rn(__dmul_rn(hi, 67108864.0), lo), 0x1p-53);
 }
 
+// The same draw truncated to its top 24 bits, as a float (exact), for the
+// FP32 kernels: 0 <= u - u24 < 2^-24, which the FP32 margin covers; no FP64
+// instruction is involved.
+__device__ __forceinline__ float plan_uniform24(uint32_t id, uint32_t t, uint32_t k0, uint32_t k1) {
+  const U4 r = philox10(id, t, 0u, 0u, k0, k1);
+  return __uint2float_rz(r.x >> 8) * 0x1p-24f;
+}
+
 // Movement order of step t: a keyed permutation of the 24-bit agent ids.
 // The step keys are the four words of Philox(seed; (0, t, 2, 0)); the id's
 // 12-bit halves (L, R) pass through four Feistel rounds

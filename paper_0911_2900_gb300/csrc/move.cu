@@ -83,24 +83,6 @@ __device__ __forceinline__ bool epoch_ends(const Ctl* ctl) {
   return ctl->claim_tag + ctl->tag_reserve > kTags || ctl->mark_stamp >= 254u;
 }
 
-// Before the movement-order pass: clear the claims and marks at the end of
-// an epoch.
-__global__ void __launch_bounds__(256) k_claim_epoch(StepArgs a) {
-  if (!epoch_ends(a.ctl)) return;
-  clear_all_claims(a, false, true);
-}
-
-// Then the step's first tag and its mark stamp.
-__global__ void k_claim_epoch_done(StepArgs a) {
-  if (threadIdx.x != 0) return;
-  if (epoch_ends(a.ctl)) {
-    a.ctl->claim_tag = 0u;
-    a.ctl->mark_stamp = 1u;
-  } else {
-    a.ctl->mark_stamp += 1u;
-  }
-}
-
 // Place of cell (x, y) in the tile-major claim arrays (16x16-cell tiles).
 __device__ __forceinline__ int claim_index(const RepDev& R, int x, int y) {
   return ((((y >> 4) * R.claim_tx) + (x >> 4)) << 8) | ((y & 15) << 4) | (x & 15);
@@ -135,8 +117,11 @@ __device__ __forceinline__ int path_cell_tab(const PathTab* t, int c0, int W, ui
 // ---------------------------------------------------------------------------
 // Footprints, priorities and first-round outcomes of all movers; agents that
 // stay, or are blocked at their first path cell by an agent that stays, need
-// no work at all.
+// no work at all.  Also clears the claims at the end of a claim epoch.
 __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
+  // a new claim epoch starts with clean claim and mark arrays (the rounds
+  // kernel then starts its tags and stamps from the beginning)
+  if (epoch_ends(a.ctl)) clear_all_claims(a, false, true);
   const int t = a.ctl->t;
   unsigned alive_local = 0, foot_local = 0;
   for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
@@ -389,8 +374,13 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   build_path_tab(&tab);
   Ctl* ctl = a.ctl;
   uint32_t nbar = 0;                     // grid barriers passed
-  uint32_t g = __ldcg(&ctl->claim_tag);  // tag of the current round
-  const uint8_t stamp = (uint8_t)__ldcg(&ctl->mark_stamp);
+  // a new epoch (claims and marks cleared by the movement-order pass) starts
+  // with tag 0 and stamp 1; every block decides alike, since nothing below
+  // changes the two counters before the last barrier
+  const bool fresh = epoch_ends(ctl);
+  uint32_t g = fresh ? 0u : __ldcg(&ctl->claim_tag);  // tag of the current round
+  const uint32_t stamp32 = fresh ? 1u : __ldcg(&ctl->mark_stamp) + 1u;
+  const uint8_t stamp = (uint8_t)stamp32;
   const uint32_t n0 = min(__ldcg(&ctl->act_count[2]), a.act_cap);
   const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const uint32_t start = (uint32_t)(((unsigned long long)n0 * b) / G);
@@ -635,6 +625,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   if (b == 0 && tid == 0) {
     // the next step's first claims use a tag below every one used so far
     ctl->claim_tag = min(g + 1u, kTags);
+    ctl->mark_stamp = stamp32;
     ctl->movers_total += (unsigned long long)n0;
     ctl->rounds_last = r;
     ctl->rounds_total += (unsigned long long)r;
@@ -687,13 +678,10 @@ __global__ void k_step_end(StepArgs a) {
   }
 }
 
-// Queues three kernels: the claim clean-up check, its bookkeeping, and the
-// movement-order pass.
+// Launched every step, even without agents: the claim clean-up must not be
+// skipped when the rounds kernel starts a new epoch.
 int move_prep_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s) {
-  if (ch.n <= 0) return 0;
-  k_claim_epoch<<<grid, 256, 0, s>>>(a);
-  k_claim_epoch_done<<<1, 32, 0, s>>>(a);
-  k_move_prep<<<grid, 256, 0, s>>>(a, ch);
+  k_move_prep<<<grid > 0 ? grid : 1, 256, 0, s>>>(a, ch);
   return 0;
 }
 

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(128) k_noalloc_plan(RepDev R, int32_t cap, int
       w[k] = wk;
       Wt += wk;
     }
-    const float r = __fmul_rn((float)plan_uniform((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi),
+    const float r = __fmul_rn(plan_uniform24((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi),
                               Wt);
     float c = 0.f, cprev = 0.f, ck = 0.f;
     int found = -1;

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
       if (sub == 0) excl = 0.f;
       const float Wt = __shfl_sync(gmask, incl, G - 1, G);
       float uf = 0.f;
-      if (sub == 0) uf = (float)plan_uniform((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
+      if (sub == 0) uf = plan_uniform24((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
       uf = __shfl_sync(gmask, uf, 0, G);
       const float r = __fmul_rn(uf, Wt);
 
@@ -329,7 +329,7 @@ __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, 
     w[k] = wk;
     Wt += wk;
   }
-  const float u = (float)plan_uniform((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
+  const float u = plan_uniform24((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
   finish_g1<K, CENTER, DIAG>(a, R, rep, slot, cell, Wt, u, norecheck, s_dxdy,
                              [&](int k) { return w[k]; });
 }
