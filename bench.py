@@ -466,29 +466,35 @@ def bench_ours(args):
     # ---- end to end through the public API with host buffers ---------------------
     # each step: place every replicate from its pinned cells-by-id array (-1:
     # left), step once, read cells and desired cells back into the same arrays
-    oc, od, live = [], [], []
-    t_step = None
-    for r in range(n_rep):
-        a = torch.empty(n0[r], dtype=torch.int32, pin_memory=True).numpy()
-        b = torch.empty(n0[r], dtype=torch.int32, pin_memory=True).numpy()
-        _, _, st = ctx.readback(r, n0[r], cells_out=a, desired_out=b)
-        t_step = st["step"]
-        oc.append(a)
-        od.append(b)
-        live.append(st["alive"])
-    h2d = 4 * sum(n0)
-    d2h = 8 * sum(n0)
+    # (one call for all replicates of a batch)
+    counts = np.array(n0, np.int32)
+    total = int(counts.sum())
+    oc = torch.empty(total, dtype=torch.int32, pin_memory=True).numpy()
+    od = torch.empty(total, dtype=torch.int32, pin_memory=True).numpy()
+    if n_rep == 1:
+        _, _, st = ctx.readback(0, n0[0], cells_out=oc, desired_out=od)
+        live = np.array([st["alive"]])
+    else:
+        _, _, live = ctx.readback_all(counts, cells_out=oc, desired_out=od)
+    _, _, st = ctx.readback(0, 0)
+    t_step = st["step"]
+    h2d = 4 * total
+    d2h = 8 * total
     e2e_agent_steps = 0
     barrier()
     torch.cuda.synchronize()
     t_e2e = time.perf_counter()
     for i in range(args.e2e_steps):
-        for r in range(n_rep):
-            ctx.place(r, oc[r], start_step=t_step)
+        if n_rep == 1:
+            ctx.place(0, oc, start_step=t_step)
+        else:
+            ctx.place_all(counts, oc, start_step=t_step)
         ctx.step(1)
-        e2e_agent_steps += sum(live)
-        for r in range(n_rep):
-            live[r] = ctx.readback(r, n0[r], cells_out=oc[r], desired_out=od[r])[2]["alive"]
+        e2e_agent_steps += int(live.sum())
+        if n_rep == 1:
+            live[0] = ctx.readback(0, n0[0], cells_out=oc, desired_out=od)[2]["alive"]
+        else:
+            _, _, live = ctx.readback_all(counts, cells_out=oc, desired_out=od)
         t_step += 1
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t_e2e

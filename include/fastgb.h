@@ -171,6 +171,15 @@ int fast_init_grid(fast_ctx* ctx, int32_t replicate, const fast_grid_desc* grid)
 int fast_place_agents(fast_ctx* ctx, int32_t replicate, int32_t n, const int32_t* cells,
                       const int32_t* ids, int32_t start_step);
 
+/* All replicates in one call (for the batched form: one upload and one wait
+ * instead of one per replicate).  counts[r] (host, [n_replicates]): number of
+ * ids of replicate r, -1 to leave it as it is; cells_by_id (host): for each
+ * replicate in order, counts[r] cells by id (-1: no agent with that id), all
+ * concatenated.  Checks as fast_place_agents; on FAST_EINVAL every replicate
+ * that failed is left without agents (the message names the first). */
+int fast_place_all(fast_ctx* ctx, const int32_t* counts, const int32_t* cells_by_id,
+                   int32_t start_step);
+
 /* Queues n_steps full steps (planning + movement) of every replicate on the
  * context's stream; returns without waiting.  Errors: FAST_ESTATE, FAST_ECUDA. */
 int fast_step(fast_ctx* ctx, int32_t n_steps);
@@ -185,6 +194,14 @@ int fast_plan_only(fast_ctx* ctx, int32_t n);
  * be NULL.  Errors: FAST_EINVAL, FAST_ETIMEOUT / FAST_ECUDA (device error). */
 int fast_readback(fast_ctx* ctx, int32_t replicate, int32_t id_bound, int32_t* cells_by_id,
                   int32_t* desired_by_id, fast_stats* stats);
+
+/* Reads every replicate back in one call (waits for the stream): for each
+ * replicate in order, counts[r] (>= 0) ids, concatenated, into cells_by_id
+ * and desired_by_id (either may be NULL; -1: not present), and alive[r] the
+ * agents of replicate r still in the simulation (may be NULL).  Errors:
+ * FAST_EINVAL, FAST_ETIMEOUT / FAST_ECUDA (device error). */
+int fast_readback_all(fast_ctx* ctx, const int32_t* counts, int32_t* cells_by_id,
+                      int32_t* desired_by_id, int32_t* alive);
 
 /* Per-step digests recorded since the last placement while FAST_OPT_DIGESTS
  * is on: sum over agents still present of splitmix64(id << 32 | cell) after

@@ -95,6 +95,9 @@ EXPORTS = {
     "fast_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "fast_plan_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "fast_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "fast_place_all": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
+    "fast_readback_all": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
     "fast_last_error": (C.c_char_p, [C.c_void_p]),
     "fast_destroy": (None, [C.c_void_p]),
     "fast_selftest_exp64": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64]),
@@ -221,6 +224,29 @@ class Context:
         self._check(self.lib.fast_place_agents(self.h, rep, len(c), _ptr(c), _ptr(i),
                                                int(start_step)), "fast_place_agents")
         self.id_bound[rep] = (int(i.max()) + 1 if len(c) else 0) if i is not None else len(c)
+
+    def place_all(self, counts, cells_by_id, start_step: int = 0):
+        """Every replicate at once: counts[r] ids of replicate r (-1: leave it),
+        cells_by_id the concatenation of the replicates' cells-by-id arrays."""
+        n = np.ascontiguousarray(counts, dtype=np.int32)
+        c = np.ascontiguousarray(cells_by_id, dtype=np.int32)
+        self._check(self.lib.fast_place_all(self.h, _ptr(n), _ptr(c), int(start_step)),
+                    "fast_place_all")
+        for r, k in enumerate(n):
+            if k >= 0:
+                self.id_bound[r] = int(k)
+
+    def readback_all(self, counts, cells_out=None, desired_out=None):
+        """(cells_by_id, desired_by_id, alive per replicate), concatenated by
+        replicate with counts[r] ids each."""
+        n = np.ascontiguousarray(counts, dtype=np.int32)
+        total = int(n.sum())
+        cells = np.empty(total, np.int32) if cells_out is None else cells_out
+        des = np.empty(total, np.int32) if desired_out is None else desired_out
+        alive = np.zeros(len(n), np.int32)
+        self._check(self.lib.fast_readback_all(self.h, _ptr(n), _ptr(cells), _ptr(des),
+                                               _ptr(alive)), "fast_readback_all")
+        return cells, des, alive
 
     def step(self, n: int = 1):
         self._check(self.lib.fast_step(self.h, int(n)), "fast_step")

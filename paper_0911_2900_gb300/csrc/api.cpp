@@ -85,6 +85,10 @@ struct fast_ctx {
   int32_t gather_cap = 0;
   uint32_t* d_id_bits = nullptr;  // 2^24-bit set of the ids a placement has seen
   int32_t* d_place_err = nullptr;  // placement check: first bad index, agents placed
+  int32_t* d_stage = nullptr;      // fast_place_all: the uploaded cells of all replicates
+  int64_t stage_cap = 0;
+  int32_t* d_place_errs = nullptr;  // fast_place_all: per replicate as d_place_err
+  int32_t err_cap = 0;
 
   struct Group {
     int v = 0;
@@ -780,6 +784,174 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->t_host = start_step;
   c->steps_since_place = 0;
+  return FAST_OK;
+}
+
+// Every replicate in one call: one upload, all checks queued, one wait.
+int fast_place_all(fast_ctx* c, const int32_t* counts, const int32_t* cells_by_id,
+                   int32_t start_step) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (!counts) return fail(c, FAST_EINVAL, "counts is NULL");
+  if (start_step < 0) return fail(c, FAST_EINVAL, "start_step < 0");
+  std::vector<int64_t> off(c->n_rep + 1, 0);
+  for (int r = 0; r < c->n_rep; ++r) {
+    const int32_t n = counts[r];
+    if (n < -1 || n > (1 << kMaxIdBits)) return fail(c, FAST_EINVAL, "replicate %d: count %d", r, n);
+    if (n >= 0 && !c->reps[r].grid_set) return fail(c, FAST_ESTATE, "grid of replicate %d not set", r);
+    off[r + 1] = off[r] + std::max(n, 0);
+  }
+  const int64_t total = off[c->n_rep];
+  if (total > 0 && !cells_by_id) return fail(c, FAST_EINVAL, "cells_by_id is NULL");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // capacities first (a reallocation changes the device descriptors)
+  for (int r = 0; r < c->n_rep; ++r) {
+    RepHost& R = c->reps[r];
+    const int32_t n = counts[r];
+    if (n < 0) continue;
+    if (R.placed && R.cap > 0)
+      LAUNCH_TRY(c, clear_occ_launch(c->d_reps + r, c->d_nslots, r, R.cap, c->stream));
+    if (n > R.cap || !R.placed) {
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      int32_t* arrs[] = {R.d.id, R.d.cell, R.d.desired, R.d.id2, R.d.cell2};
+      for (auto p : arrs) dfree(c, p);
+      dfree(c, R.d.prio);
+      dfree(c, R.d.mvinfo);
+      const int32_t cap = std::max(n, std::max(R.cap, 1));
+      if (int e = alloc_into(c, &R.d.id, cap)) return e;
+      if (int e = alloc_into(c, &R.d.cell, cap)) return e;
+      if (int e = alloc_into(c, &R.d.desired, cap)) return e;
+      if (int e = alloc_into(c, &R.d.id2, cap)) return e;
+      if (int e = alloc_into(c, &R.d.cell2, cap)) return e;
+      if (int e = alloc_into(c, &R.d.prio, cap)) return e;
+      if (int e = alloc_into(c, &R.d.mvinfo, cap)) return e;
+      R.cap = cap;
+      R.d.cap = cap;
+      c->layout_dirty = true;
+    }
+    R.placed = true;
+  }
+  if (c->layout_dirty)
+    if (int e = rebuild_layout(c)) return e;
+  if (total > c->stage_cap) {
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    dfree(c, c->d_stage);
+    c->d_stage = nullptr;
+    if (int e = alloc_into(c, &c->d_stage, (size_t)total)) return e;
+    c->stage_cap = total;
+  }
+  if (c->err_cap < 2 * c->n_rep) {
+    dfree(c, c->d_place_errs);
+    c->d_place_errs = nullptr;
+    if (int e = alloc_into(c, &c->d_place_errs, (size_t)2 * c->n_rep)) return e;
+    c->err_cap = 2 * c->n_rep;
+  }
+  if (total > 0)
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_stage, cells_by_id, (size_t)total * 4,
+                                cudaMemcpyHostToDevice, c->stream));
+  std::vector<int32_t> res(2 * c->n_rep);
+  for (int r = 0; r < c->n_rep; ++r) {
+    res[2 * r] = INT32_MAX;
+    res[2 * r + 1] = 0;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_place_errs, res.data(), res.size() * 4, cudaMemcpyHostToDevice,
+                              c->stream));
+  for (int r = 0; r < c->n_rep; ++r) {
+    RepHost& R = c->reps[r];
+    if (counts[r] < 0) continue;
+    CUDA_TRY(c, cudaMemsetAsync(R.d.cell, 0xFF, (size_t)R.cap * 4, c->stream));
+    LAUNCH_TRY(c, place_checked_launch(c->d_reps + r, c->d_stage + off[r], nullptr, counts[r],
+                                       (long long)R.W * R.H, nullptr,
+                                       reinterpret_cast<uint8_t*>(R.d.mvinfo),
+                                       c->d_place_errs + 2 * r, c->stream));
+  }
+  std::vector<int32_t> slots(c->n_rep), exited(c->n_rep);
+  CUDA_TRY(c, cudaMemcpyAsync(res.data(), c->d_place_errs, res.size() * 4, cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(slots.data(), c->d_nslots, 4 * c->n_rep, cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(exited.data(), c->d_exited, 4 * c->n_rep, cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  int first_bad = -1;
+  for (int r = 0; r < c->n_rep; ++r) {
+    if (counts[r] < 0) continue;
+    RepHost& R = c->reps[r];
+    exited[r] = 0;
+    if (res[2 * r] != INT32_MAX) {
+      LAUNCH_TRY(c, place_rollback_launch(c->d_reps + r, c->d_stage + off[r], counts[r],
+                                          reinterpret_cast<uint8_t*>(R.d.mvinfo), c->stream));
+      slots[r] = 0;
+      R.n = 0;
+      if (first_bad < 0) first_bad = r;
+    } else {
+      slots[r] = counts[r];
+      R.n = res[2 * r + 1];
+    }
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots, slots.data(), 4 * c->n_rep, cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_exited, exited.data(), 4 * c->n_rep, cudaMemcpyHostToDevice,
+                              c->stream));
+  const int32_t zero = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->t, &start_step, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->dig_count, &zero, 4, cudaMemcpyHostToDevice, c->stream));
+  const StepArgs a = args_of(c);
+  LAUNCH_TRY(c, step_begin_launch(a, c->stream));
+  c->resort_pending = true;
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->t_host = start_step;
+  c->steps_since_place = 0;
+  if (first_bad >= 0) {
+    const int32_t i = res[2 * first_bad];
+    return fail(c, FAST_EINVAL,
+                "replicate %d, agent %d: cell %d is outside, not free, unreachable, an exit or "
+                "taken; the replicates that failed now have no agents",
+                first_bad, i, cells_by_id[off[first_bad] + i]);
+  }
+  return FAST_OK;
+}
+
+int fast_readback_all(fast_ctx* c, const int32_t* counts, int32_t* cells_by_id,
+                      int32_t* desired_by_id, int32_t* alive) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (!counts) return fail(c, FAST_EINVAL, "counts is NULL");
+  std::vector<int64_t> off(c->n_rep + 1, 0);
+  for (int r = 0; r < c->n_rep; ++r) {
+    if (counts[r] < 0) return fail(c, FAST_EINVAL, "replicate %d: count %d", r, counts[r]);
+    off[r + 1] = off[r] + counts[r];
+  }
+  const int64_t total = off[c->n_rep];
+  if (int e = check_device_error(c)) return e;
+  if (total > 0 && (cells_by_id || desired_by_id)) {
+    if (total * 2 > c->gather_cap) {
+      dfree(c, c->d_gather);
+      c->d_gather = nullptr;
+      if (int e = alloc_into(c, &c->d_gather, (size_t)total * 2)) return e;
+      c->gather_cap = total * 2;
+    }
+    CUDA_TRY(c, cudaMemsetAsync(c->d_gather, 0xFF, (size_t)total * 8, c->stream));
+    for (int r = 0; r < c->n_rep; ++r) {
+      RepHost& R = c->reps[r];
+      if (!R.placed || counts[r] == 0) continue;
+      LAUNCH_TRY(c, gather_by_id_launch(c->d_reps + r, c->d_nslots, r, R.cap,
+                                        c->d_gather + off[r], c->d_gather + total + off[r],
+                                        counts[r], c->stream));
+    }
+    if (cells_by_id)
+      CUDA_TRY(c, cudaMemcpyAsync(cells_by_id, c->d_gather, (size_t)total * 4,
+                                  cudaMemcpyDeviceToHost, c->stream));
+    if (desired_by_id)
+      CUDA_TRY(c, cudaMemcpyAsync(desired_by_id, c->d_gather + total, (size_t)total * 4,
+                                  cudaMemcpyDeviceToHost, c->stream));
+  }
+  std::vector<int32_t> exited(c->n_rep);
+  CUDA_TRY(c, cudaMemcpyAsync(exited.data(), c->d_exited, 4 * c->n_rep, cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (alive)
+    for (int r = 0; r < c->n_rep; ++r) alive[r] = c->reps[r].placed ? c->reps[r].n - exited[r] : 0;
   return FAST_OK;
 }
 

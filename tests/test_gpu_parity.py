@@ -240,6 +240,35 @@ def test_autotune_cache_roundtrip(fg, tmp_path):
         ctx.autotune(trials=0)
 
 
+def test_place_all_and_readback_all_match_per_replicate_calls(fg, orc):
+    """Placing and reading every replicate in one call gives the same
+    trajectories as the per-replicate calls (and the oracle); a bad cell in
+    one replicate empties only the replicates that failed."""
+    works = wl.config_batch(n_rep=4, seed=5, cells_hi=200 ** 2, agents_hi=3000)
+    steps = 12
+    ctx = fg.Context(len(works), "fp32_recheck")
+    for r, w in enumerate(works):
+        ctx.init_grid(r, w.cell_type, w.k_S, w.v_m, w.seed)
+    counts = np.array([len(w.cells) for w in works], np.int32)
+    ctx.place_all(counts, np.concatenate([w.cells for w in works]))
+    ctx.step(6)
+    cells, des, alive = ctx.readback_all(counts)
+    ctx.place_all(counts, cells, start_step=6)       # the read-back state, placed again
+    ctx.step(6)
+    cells, des, alive = ctx.readback_all(counts)
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for r, w in enumerate(works):
+        o = run_oracle(orc, w, steps)
+        assert np.array_equal(cells[off[r]:off[r + 1]], o["cells"])
+        assert alive[r] == int((o["cells"] >= 0).sum())
+    bad = cells.copy()
+    bad[off[2]] = 0                                    # a wall (the top-left corner)
+    with pytest.raises(fg.FastError):
+        ctx.place_all(counts, bad, start_step=12)
+    _, _, alive = ctx.readback_all(counts)
+    assert alive[2] == 0 and alive[0] == int((cells[off[0]:off[1]] >= 0).sum())
+
+
 def test_batched_replicates(fg, orc):
     works = wl.config_batch(n_rep=6, seed=3, cells_hi=300 ** 2, agents_hi=6000)
     steps = 30
