@@ -51,6 +51,7 @@ L2_FLUSH_BYTES = 512 << 20
 KERNEL_SOURCES = {
     "k_plan_tile": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
     "k_plan_fp32": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
+    "k_plan_direct": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
     "k_move_rounds": ["move.cu", "fast_device.cuh", "fast_internal.h"],
 }
 
@@ -448,7 +449,7 @@ def bench_ours(args):
     # the planning kernel the tuned context runs for v_m = 4 (or its only v_m)
     v_main = 4 if any(w.v_m == 4 for w in works) else works[0].v_m
     lanes_main = tune["lanes"][v_main - 1] if tune is not None else 0
-    plan_kernel = "k_plan_tile" if lanes_main == 0 else "k_plan_fp32"
+    plan_kernel = {0: "k_plan_tile", 1: "k_plan_direct"}.get(lanes_main, "k_plan_fp32")
 
     # ---- the all-FP64 form ------------------------------------------------------
     ctx64 = make_ctx("fp64")

@@ -4,7 +4,8 @@
 // Sec. 2: k_S = 1.2, k_other = 0).
 //
 //   k_plan_tile<V,REACH>    one thread per agent, per-warp record tiles
-//   k_plan_fp32<V,REACH,G>  G lanes per agent; FP32 weights exp(-k_S dS) on
+//   k_plan_direct<V,REACH>  one thread per agent, records through L1
+//   k_plan_fp32<V,REACH,G>  G = 2, 4, 8 lanes per agent; FP32 weights exp(-k_S dS) on
 //                           the SFU, shuffle prefix sums over the G lanes,
 //                           Philox draw, margin test; draws that fall within
 //                           the margin of a cumulative boundary go to a queue
@@ -334,6 +335,29 @@ __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, 
                              [&](int k) { return w[k]; });
 }
 
+// ---------------------------------------------------------------------------
+// FP32 planning, one thread per agent (the 1-lane variant), candidate records
+// read through L1 at compile-time offsets from row pointers; same weights,
+// margin and outputs as the other variants.
+template <int V, int REACH, bool DIAG>
+__global__ void __launch_bounds__(256) k_plan_direct(StepArgs a, Chunks ch, int norecheck) {
+  __shared__ int s_dxdy[reach_count(V, REACH)];
+  fill_dxdy<V, REACH>(s_dxdy);
+  __syncthreads();
+  const int t = a.ctl->t;
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const RepDev& R = a.reps[rep];
+    const int end = min(ch.begin[c] + kChunk, a.n_slots[rep]);
+    const int slot = ch.begin[c] + threadIdx.x;
+    if (slot >= end) continue;
+    const int cell = R.cell[slot];
+    if (cell < 0) continue;
+    plan_one_g1<V, REACH, DIAG, false>(a, R, rep, slot, cell, R.rec + cell, R.W, t, norecheck,
+                                       s_dxdy);
+  }
+}
+
 template <int V, int REACH, bool DIAG>
 __global__ void __launch_bounds__(256, 2) k_plan_tile(StepArgs a, Chunks ch, int norecheck) {
   extern __shared__ __align__(16) uint32_t s_tiles[];
@@ -546,7 +570,13 @@ static int launch_fp32(const StepArgs& a, int lanes, const Chunks& ch, int grid,
       k_plan_fp32<V, REACH, G, false><<<grid, 256, 0, s>>>(a, ch, norecheck);      \
     return 0;                                                                      \
   }
-  FAST_L(1)
+  if (lanes == 1) {
+    if (diag)
+      k_plan_direct<V, REACH, true><<<grid, 256, 0, s>>>(a, ch, norecheck);
+    else
+      k_plan_direct<V, REACH, false><<<grid, 256, 0, s>>>(a, ch, norecheck);
+    return 0;
+  }
   FAST_L(2)
   FAST_L(4)
   FAST_L(8)
