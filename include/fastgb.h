@@ -71,8 +71,8 @@ extern "C" {
 #define FAST_OPT_DIGESTS 2        /* 1: record per-step digests (fast_get_digests)  */
 #define FAST_OPT_LANES_V1 3       /* FP32 planning kernel for v_m=1 (..._V1 + v_m - 1 */
                                   /* for v_m = 1..5): 0 one thread per agent with   */
-                                  /* per-warp record tiles (default); 1 one thread  */
-                                  /* per agent reading records through L1; 2, 4, 8  */
+                                  /* per-warp record tiles; 1 one thread per agent  */
+                                  /* reading records through L1 (default); 2, 4, 8  */
                                   /* lanes per agent with shuffle prefix sums       */
 #define FAST_OPT_BARRIER_NS 10    /* time limit of one device-side wait, ns         */
 #define FAST_OPT_USE_GRAPH 11     /* 1 (default): steps replay a captured CUDA graph */

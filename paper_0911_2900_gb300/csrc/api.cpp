@@ -32,7 +32,7 @@ namespace {
 // measured maximum of ex2.approx.ftz.f32 over the argument range with a
 // factor of two to spare; see the self test fast_selftest_ex2).
 constexpr double kEx2RelErr = 0x1p-21;
-constexpr int kDefaultLanes[5] = {0, 0, 0, 0, 0};  // 0: per-warp record tiles
+constexpr int kDefaultLanes[5] = {1, 1, 1, 1, 1};  // 1: one thread per agent, records via L1
 constexpr double kSqrt2 = 1.4142135623730951;
 constexpr double kLn2 = 0.6931471805599453;
 constexpr double kLog2e = 1.4426950408889634;
@@ -119,7 +119,7 @@ struct fast_ctx {
   // options
   int resort_period = 8;
   bool digests = false;
-  int lanes[5] = {1, 2, 2, 4, 4};
+  int lanes[5] = {1, 1, 1, 1, 1};
   long long barrier_ns = 2000000000ll;
   bool use_graph = true;
   int move_blocks = 0;
