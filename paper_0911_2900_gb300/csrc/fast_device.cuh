@@ -193,6 +193,24 @@ __device__ __forceinline__ float ds32(int da, int db) {
   return __fmaf_rn(fb, 0x1.9fcef4p-26f, t1);
 }
 
+
+// The same from a raw record: the 15-bit fields become exact floats through
+// the 2^23 exponent (0x4B000000 | v is the float 2^23 + v), so that the
+// differences a - a0 and b - b0 are float subtractions of exact integers;
+// a0m = 2^23 + a0 and b0m = 2^23 + b0 are the agent's own fields likewise.
+// Identical values to ds32(a - a0, b - b0).
+__device__ __forceinline__ float ds32_rec(uint32_t r, float a0m, float b0m) {
+  const float fa = __fsub_rn(__uint_as_float((r & 0x7FFFu) | 0x4B000000u), a0m);
+  const float fb = __fsub_rn(__uint_as_float(((r >> 15) & 0x7FFFu) | 0x4B000000u), b0m);
+  const float t1 = __fmaf_rn(fb, 0x1.6a09e6p+0f, fa);
+  return __fmaf_rn(fb, 0x1.9fcef4p-26f, t1);
+}
+
+// 2^23 + v as a float (exact for 0 <= v < 2^23).
+__device__ __forceinline__ float field_m(int v) {
+  return __uint_as_float(0x4B000000u | (uint32_t)v);
+}
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -88,8 +88,8 @@ __device__ __forceinline__ void fill_dxdy(int* s_dxdy) {
 }
 
 // FP32 weight of a candidate record seen from (a0, b0): 0 if blocked.
-__device__ __forceinline__ float rec_weight(uint32_t r, int a0, int b0, float c32) {
-  return (r & REC_OCC) ? 0.f : ex2_approx(ds32(rec_a(r) - a0, rec_b(r) - b0) * c32);
+__device__ __forceinline__ float rec_weight(uint32_t r, float a0m, float b0m, float c32) {
+  return (r & REC_OCC) ? 0.f : ex2_approx(ds32_rec(r, a0m, b0m) * c32);
 }
 
 // Shared end of the one-thread kernels: the draw against the cumulative
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
         const bool adm = (k < K) && (k != CENTER) && mask_bit(m0, m1, k);
         rr[j] = adm ? rec[cell + s_off[k]] : REC_OCC;
       }
-      const int a0 = rec_a(rec0), b0 = rec_b(rec0);
+      const float a0m = field_m(rec_a(rec0)), b0m = field_m(rec_b(rec0));
       float w[Q];
       float lsum = 0.f;
 #pragma unroll
@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
         if (k == CENTER) {
           wk = 1.0f;
         } else if (!(rr[j] & REC_OCC)) {
-          wk = ex2_approx(ds32(rec_a(rr[j]) - a0, rec_b(rr[j]) - b0) * c32);
+          wk = ex2_approx(ds32_rec(rr[j], a0m, b0m) * c32);
         }
         w[j] = wk;
         lsum += wk;
@@ -320,13 +320,13 @@ __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, 
     const bool adm = (k != CENTER) && mask_bit(m0, m1, k);
     rr[k] = adm ? p0[off] : REC_OCC;
   }
-  const int a0 = rec_a(rec0), b0 = rec_b(rec0);
+  const float a0m = field_m(rec_a(rec0)), b0m = field_m(rec_b(rec0));
   const float c32 = R.c32;
   float w[K];
   float Wt = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const float wk = (k == CENTER) ? 1.0f : rec_weight(rr[k], a0, b0, c32);
+    const float wk = (k == CENTER) ? 1.0f : rec_weight(rr[k], a0m, b0m, c32);
     w[k] = wk;
     Wt += wk;
   }
