@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
   const uint32_t start = (uint32_t)(((unsigned long long)n0 * b) / G);
   const uint32_t nb = (uint32_t)(((unsigned long long)n0 * (b + 1)) / G) - start;
+  const MoverLists sm = smem_lists(dsm);  // the block's shared-memory lists
   MoverLists gl;  // the block's slice of global memory
   gl.P = a.mv_prio + start;
   gl.C0 = a.mv_c0 + start;
@@ -418,7 +419,7 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
   if (!grid_barrier(ctl, nbar)) return;
 
   // ---- round 0: the ones that must wait claim for round 1 and go to the
-  // block's global staging area
+  // block's lists (shared memory first, global memory beyond its capacity)
   for (uint32_t k = tid; k < nb; k += blockDim.x) {
     const MoveEntry e = a.act[2][start + k];
     const int rep = (int)(e.ref >> 24), slot = (int)(e.ref & 0xFFFFFFu);
@@ -449,26 +450,27 @@ __global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
           if (s <= n) atomicMin(&nxt[q[s]], v);
       }
       const uint32_t j = append_slot(&s_cnt[1]);
-      gl.P[j] = e.prio;
-      gl.C0[j] = e.c0;
-      gl.RF[j] = e.ref;
-      gl.IN[j] = (e.info & ~(0x3Fu << MV_NEED)) | (need << MV_NEED);
+      const MoverLists& dst = j < (uint32_t)kMoveSmemCap ? sm : gl;
+      dst.P[j] = e.prio;
+      dst.C0[j] = e.c0;
+      dst.RF[j] = e.ref;
+      dst.IN[j] = (e.info & ~(0x3Fu << MV_NEED)) | (need << MV_NEED);
     }
   }
   __syncthreads();
   const uint32_t w0 = s_cnt[1];
-  // the waiting movers to shared memory when they fit (a block's choice)
+  // the waiting movers stay in shared memory when they all fit there (a
+  // block's choice); else the first kMoveSmemCap join the rest in global
   const bool in_smem = w0 <= (uint32_t)kMoveSmemCap;
-  MoverLists ml = in_smem ? smem_lists(dsm) : gl;
-  for (uint32_t k = tid; k < w0; k += blockDim.x) {
-    if (in_smem) {
-      ml.P[k] = gl.P[k];
-      ml.C0[k] = gl.C0[k];
-      ml.RF[k] = gl.RF[k];
-      ml.IN[k] = gl.IN[k];
+  if (!in_smem)
+    for (uint32_t k = tid; k < (uint32_t)kMoveSmemCap; k += blockDim.x) {
+      gl.P[k] = sm.P[k];
+      gl.C0[k] = sm.C0[k];
+      gl.RF[k] = sm.RF[k];
+      gl.IN[k] = sm.IN[k];
     }
-    ml.L1[k] = k;
-  }
+  MoverLists ml = in_smem ? sm : gl;
+  for (uint32_t k = tid; k < w0; k += blockDim.x) ml.L1[k] = k;
   if (tid == 0 && w0) atomicAdd(&ctl->wait_count[1], w0);
   if (tid == 0) {
     atomicMax(&ctl->phase_ns[0], global_ns() - t_start);
