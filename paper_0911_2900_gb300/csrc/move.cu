@@ -122,82 +122,121 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
   // a new claim epoch starts with clean claim and mark arrays (the rounds
   // kernel then starts its tags and stamps from the beginning)
   if (epoch_ends(a.ctl)) clear_all_claims(a, false, true);
+  __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_base;
   const int t = a.ctl->t;
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned alive_local = 0, foot_local = 0;
-  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {  // the same chunks for the whole block
     const int rep = ch.rep[c];
     const RepDev& R = a.reps[rep];
     const int end = min(ch.begin[c] + kChunk, a.n_slots[rep]);
     const int slot = ch.begin[c] + threadIdx.x;
-    if (slot >= end) continue;
-    const int cell = R.cell[slot];
-    if (cell < 0) continue;
-    ++alive_local;
-    const int des = R.desired[slot];
-    if (des == cell) continue;
-    const int W = R.W;
-    const int x0 = cell % W, y0 = cell / W;
-    const int dx = des % W - x0, dy = des / W - y0;
-    const int L = max(abs(dx), abs(dy));
-    // all path records first (independent loads), then the scan
-    uint32_t pr[6];
+    const int cell = slot < end ? R.cell[slot] : -1;
+    // the step's movement-order keys (one Philox block per warp, shared)
+    U4 k;
+    if (lane == 0) k = move_step_keys((uint32_t)t, R.seed_lo, R.seed_hi);
+    k.x = __shfl_sync(0xffffffffu, k.x, 0);
+    k.y = __shfl_sync(0xffffffffu, k.y, 0);
+    k.z = __shfl_sync(0xffffffffu, k.z, 0);
+    k.w = __shfl_sync(0xffffffffu, k.w, 0);
+    bool mover = false;
+    MoveEntry e;
+    if (cell >= 0) {
+      ++alive_local;
+      const int des = R.desired[slot];
+      const int W = R.W;
+      const int x0 = cell % W, y0 = cell / W;
+      const int dx = des % W - x0, dy = des / W - y0;
+      const int L = max(abs(dx), abs(dy));
+      // all path records first (independent loads), then the scan
+      uint32_t pr[6];
 #pragma unroll
-    for (int s = 1; s <= 5; ++s)
-      pr[s] = (s <= L) ? R.rec[(y0 + div_half_away(s * dy, L)) * W +
-                               (x0 + div_half_away(s * dx, L))]
-                       : REC_STA;
-    int fp = 0;
-    uint32_t ex = 0;
+      for (int s = 1; s <= 5; ++s)
+        pr[s] = (s <= L) ? R.rec[(y0 + div_half_away(s * dy, L)) * W +
+                                 (x0 + div_half_away(s * dx, L))]
+                         : REC_STA;
+      int fp = 0;
+      uint32_t ex = 0;
 #pragma unroll
-    for (int s = 1; s <= 5; ++s) {
-      const uint32_t r = pr[s];
-      if (s > L || (r & REC_STA)) break;
-      if (rec_exit(r)) {
-        ex = MV_EXIT;
-        break;
-      }
-      fp = s;
-    }
-    if (fp == 0 && !ex) continue;
-    // the walk if nobody touches the footprint first: up to the first
-    // occupied cell, or into an exit
-    int fin = 0;
-    bool gone = false, stop = false;
-#pragma unroll
-    for (int s = 1; s <= 5; ++s) {
-      const uint32_t r = pr[s];
-      stop = stop || s > L || (r & REC_OCC);
-      if (!stop) {
-        fin = s;
+      for (int s = 1; s <= 5; ++s) {
+        const uint32_t r = pr[s];
+        if (s > L || (r & REC_STA)) break;
         if (rec_exit(r)) {
-          gone = true;
-          stop = true;
+          ex = MV_EXIT;
+          break;
         }
+        fp = s;
+      }
+      if (fp > 0 || ex) {
+        // the walk if nobody touches the footprint first: up to the first
+        // occupied cell, or into an exit
+        int fin = 0;
+        bool gone = false, stop = false;
+#pragma unroll
+        for (int s = 1; s <= 5; ++s) {
+          const uint32_t r = pr[s];
+          stop = stop || s > L || (r & REC_OCC);
+          if (!stop) {
+            fin = s;
+            if (rec_exit(r)) {
+              gone = true;
+              stop = true;
+            }
+          }
+        }
+        foot_local += (unsigned)fp + 1u;
+        e.c0 = ((uint32_t)y0 << 16) | (uint32_t)x0;
+        e.ref = ((uint32_t)rep << 24) | (uint32_t)slot;
+        e.prio = move_priority((uint32_t)R.id[slot], k);
+        e.info = (uint32_t)fp | ex | ((uint32_t)(dx + 8) << MV_DX) |
+                 ((uint32_t)(dy + 8) << MV_DY) | ((uint32_t)fin << MV_FIN) |
+                 (gone ? MV_GONE : 0u);
+        mover = true;
       }
     }
-    foot_local += (unsigned)fp + 1u;
-    const U4 k = move_step_keys((uint32_t)t, R.seed_lo, R.seed_hi);
-    const uint32_t prio = move_priority((uint32_t)R.id[slot], k);
-    const uint32_t i = append_slot(&a.ctl->act_count[2]);
-    if (i < a.act_cap) {
-      MoveEntry e;
-      e.c0 = ((uint32_t)y0 << 16) | (uint32_t)x0;
-      e.ref = ((uint32_t)rep << 24) | (uint32_t)slot;
-      e.prio = prio;
-      e.info = (uint32_t)fp | ex | ((uint32_t)(dx + 8) << MV_DX) | ((uint32_t)(dy + 8) << MV_DY) |
-               ((uint32_t)fin << MV_FIN) | (gone ? MV_GONE : 0u);
-      a.act[2][i] = e;
+    // the chunk's movers in one block-wide reservation of the mover list
+    const unsigned bal = __ballot_sync(0xffffffffu, mover);
+    if (lane == 0) s_warp[wid] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t sum = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        const uint32_t x = s_warp[w];
+        s_warp[w] = sum;
+        sum += x;
+      }
+      s_base = sum ? atomicAdd(&a.ctl->act_count[2], sum) : 0u;
     }
+    __syncthreads();
+    if (mover) {
+      const uint32_t i = s_base + s_warp[wid] + __popc(bal & ((1u << lane) - 1u));
+      if (i < a.act_cap) a.act[2][i] = e;
+    }
+    __syncthreads();
   }
   // agents alive at the start of the step, footprint cells of the movers
   for (int o = 16; o > 0; o >>= 1) {
     alive_local += __shfl_xor_sync(0xffffffffu, alive_local, o);
     foot_local += __shfl_xor_sync(0xffffffffu, foot_local, o);
   }
-  if ((threadIdx.x & 31) == 0 && alive_local)
-    atomicAdd(&a.ctl->agent_steps, (unsigned long long)alive_local);
-  if ((threadIdx.x & 31) == 0 && foot_local)
-    atomicAdd(&a.ctl->foot_total, (unsigned long long)foot_local);
+  if (lane == 0) {
+    s_warp[wid] = alive_local;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long al = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) al += s_warp[w];
+    if (al) atomicAdd(&a.ctl->agent_steps, al);
+  }
+  __syncthreads();
+  if (lane == 0) s_warp[wid] = foot_local;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long fo = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) fo += s_warp[w];
+    if (fo) atomicAdd(&a.ctl->foot_total, fo);
+  }
 }
 
 // ---------------------------------------------------------------------------
