@@ -386,7 +386,7 @@ int plan_grid(fast_ctx* c, int n_chunks) { return std::max(1, std::min(n_chunks,
 // (the rounds are latency-bound), capped by the work and by the option.
 int move_grid(fast_ctx* c) {
   int g = 0;
-  if (move_rounds_max_grid(1024, &g) != 0 || g <= 0) g = c->sms;
+  if (move_rounds_max_grid(kMoveThreads, &g) != 0 || g <= 0) g = c->sms;
   if (c->move_blocks > 0) g = std::min(g, c->move_blocks);
   return std::max(g, 1);
 }
@@ -425,7 +425,7 @@ int enqueue_step(fast_ctx* c, bool resort) {
   if (c->digests) LAUNCH_TRY(c, digest_des_launch(a, all, plan_grid(c, all.n), c->cur));
   LAUNCH_TRY(c, move_prep_launch(a, all, plan_grid(c, all.n), c->cur));
   CUDA_TRY(c, record_event(c, 3));
-  LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), 1024, c->cur));
+  LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), kMoveThreads, c->cur));
   CUDA_TRY(c, record_event(c, 4));
   if (c->digests) {
     LAUNCH_TRY(c, digest_cell_launch(a, all, plan_grid(c, all.n), c->cur));

@@ -17,8 +17,8 @@ constexpr int kMaxK = 121;          // largest reach set (L-infinity, v_m = 5)
 constexpr int kDevErrTimeout = 5;   // device error: a bounded wait gave up
 constexpr int kDevErrRounds = 6;    // device error: movement rounds exceeded the bound
 constexpr int kRoundLog = 64;       // movement rounds recorded per step
-constexpr int kMoveThreads = 1024;  // threads per block of the movement rounds
-constexpr int kMoveSmemCap = 9000;  // movers per block kept in shared memory (24 B each)
+constexpr int kMoveThreads = 512;   // threads per block of the movement rounds (2 per SM)
+constexpr int kMoveSmemCap = 4500;  // movers per block kept in shared memory (24 B each)
 
 // One mover of the current step (16 bytes): start cell, (replicate << 24 |
 // slot), movement priority, footprint info.

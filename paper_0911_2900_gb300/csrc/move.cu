@@ -405,7 +405,7 @@ __device__ __forceinline__ void claim_list(const StepArgs& a, const PathTab* tab
   }
 }
 
-__global__ void __launch_bounds__(kMoveThreads, 1) k_move_rounds(StepArgs a) {
+__global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ PathTab tab;
   __shared__ uint32_t s_cnt[2];
