@@ -314,11 +314,23 @@ __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, 
   const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
   const unsigned long long m1 = (K > 64) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
   uint32_t rr[K];
+  // a warp whose agents see every candidate (no wall in sight, inside the
+  // grid) skips the per-candidate mask tests
+  constexpr unsigned long long kFull0 = K >= 64 ? ~0ull : ((1ull << K) - 1ull);
+  constexpr unsigned long long kFull1 = K > 64 ? ((1ull << (K - 64)) - 1ull) : 0ull;
+  if (__all_sync(__activemask(), m0 == kFull0 && m1 == kFull1)) {
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    const int off = TILE ? (T.dy[k] * kTileP + T.dx[k]) : (T.dy[k] * pitch + T.dx[k]);
-    const bool adm = (k != CENTER) && mask_bit(m0, m1, k);
-    rr[k] = adm ? p0[off] : REC_OCC;
+    for (int k = 0; k < K; ++k) {
+      const int off = TILE ? (T.dy[k] * kTileP + T.dx[k]) : (T.dy[k] * pitch + T.dx[k]);
+      rr[k] = (k != CENTER) ? p0[off] : REC_OCC;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int off = TILE ? (T.dy[k] * kTileP + T.dx[k]) : (T.dy[k] * pitch + T.dx[k]);
+      const bool adm = (k != CENTER) && mask_bit(m0, m1, k);
+      rr[k] = adm ? p0[off] : REC_OCC;
+    }
   }
   const float a0m = field_m(rec_a(rec0)), b0m = field_m(rec_b(rec0));
   const float c32 = R.c32;
