@@ -66,11 +66,12 @@ def source_digest(kernel):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel, workload_name):
+def measured_traffic(kernel, workload_name, profiles_dir=None):
     """dram__bytes_read.sum + dram__bytes_write.sum per launch from the
     committed ncu summary of this kernel on this workload, or None when there
     is none or the kernel's sources changed since it was taken."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload_name}.md")
+    path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"),
+                        f"{kernel}_{workload_name}.md")
     try:
         fields = {}
         with open(path) as fh:
@@ -217,7 +218,8 @@ def max_over_ranks(x, world, op="max"):
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([float(x)], dtype=torch.float64, device="cuda")
+    device = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
 
