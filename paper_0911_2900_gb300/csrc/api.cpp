@@ -339,7 +339,8 @@ int rebuild_layout(fast_ctx* c) {
       if (int e = alloc_into(c, &p, n)) return e;
     c->list_cap = (uint32_t)total_cap;
   }
-  const size_t words = (size_t)bucket_base + 1 + 2 * (size_t)c->n_rep;
+  // bucket offsets, 2 words per replicate, the scan's block sums (<= 1024)
+  const size_t words = (size_t)bucket_base + 1 + 2 * (size_t)c->n_rep + 1024;
   if (words > c->bucket_words) {
     dfree(c, c->d_bucket);
     c->d_bucket = nullptr;
@@ -433,7 +434,7 @@ int enqueue_step(fast_ctx* c, bool resort) {
   }
   if (resort) {
     LAUNCH_TRY(c, resort_launch(a, all, plan_grid(c, all.n), false, c->cur));
-    c->launches += 5;  // resort_launch queues six kernels
+    c->launches += 7;  // resort_launch queues eight kernels
   }
   LAUNCH_TRY(c, step_end_launch(a, c->cur));
   CUDA_TRY(c, record_event(c, 5));
@@ -545,7 +546,7 @@ int sort_if_pending(fast_ctx* c) {
   const StepArgs a = args_of(c);
   const Chunks all = all_chunks(c);
   LAUNCH_TRY(c, resort_launch(a, all, plan_grid(c, all.n), true, c->stream));
-  c->launches += 5;
+  c->launches += 7;
   c->resort_pending = false;
   return FAST_OK;
 }
@@ -1102,7 +1103,7 @@ int apply_shift(fast_ctx* c, int shift) {
   const StepArgs a = args_of(c);
   const Chunks all = all_chunks(c);
   LAUNCH_TRY(c, resort_launch(a, all, plan_grid(c, all.n), true, c->stream));
-  c->launches += 5;
+  c->launches += 7;
   c->resort_pending = false;
   return FAST_OK;
 }

@@ -2,6 +2,8 @@
 // placement, Morton re-sort with compaction of agents that left, digests,
 // read-back gathers, the reach-union counter used for byte accounting, and
 // the kernels behind the library's self-test entry points.
+#include <algorithm>
+
 #include "fast_device.cuh"
 
 namespace fastgb {
@@ -186,38 +188,90 @@ __global__ void k_bucket_count(StepArgs a, Chunks ch) {
   }
 }
 
-// One block: exclusive scan of the bucket counts (in place), then the number
-// of agents of each replicate (= its new slot count).
-__global__ void __launch_bounds__(1024) k_bucket_scan(StepArgs a) {
-  __shared__ uint32_t s_part[1024];
-  const int n = a.n_buckets;
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int lo = min(n, (int)threadIdx.x * per), hi = min(n, lo + per);
+// Exclusive scan of the bucket counts in place, in three launches: every
+// block sums its range of buckets (coalesced), then every block scans its
+// range in tiles of 1024 starting from the sum of the blocks before it, then
+// one block derives each replicate's first offset and new agent count.  The
+// block sums live after the per-replicate words of the bucket array.
+constexpr int kScanThreads = 1024;
+constexpr int kScanMaxBlocks = 1024;
+
+__device__ __forceinline__ uint32_t* scan_parts(const StepArgs& a) {
+  return a.bucket_count + a.n_buckets + 1 + 2 * a.n_rep;
+}
+
+__device__ __forceinline__ void scan_range(int n, int b, int nb, int* lo, int* hi) {
+  const int per = ((n + nb - 1) / nb + kScanThreads - 1) / kScanThreads * kScanThreads;
+  *lo = min(n, b * per);
+  *hi = min(n, *lo + per);
+}
+
+// Block-wide inclusive scan of one value per thread (kScanThreads threads).
+__device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
+  }
+  if (lane == 31) s_warp[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    uint32_t w = s_warp[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    s_warp[lane] = w;
+  }
+  __syncthreads();
+  const uint32_t add = wid > 0 ? s_warp[wid - 1] : 0u;
+  __syncthreads();
+  return v + add;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_bucket_scan_parts(StepArgs a) {
+  __shared__ uint32_t s_warp[32];
+  int lo, hi;
+  scan_range(a.n_buckets, blockIdx.x, gridDim.x, &lo, &hi);
   uint32_t sum = 0;
-  for (int i = lo; i < hi; ++i) sum += a.bucket_count[i];
-  s_part[threadIdx.x] = sum;
+  for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) sum += a.bucket_count[i];
+  const uint32_t tot = block_incl_scan(sum, s_warp);
+  if (threadIdx.x == blockDim.x - 1) scan_parts(a)[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_bucket_scan_apply(StepArgs a) {
+  __shared__ uint32_t s_warp[32];
+  __shared__ uint32_t s_run;
+  const uint32_t* parts = scan_parts(a);
+  // the sum of the blocks before this one
+  const uint32_t before = threadIdx.x < blockIdx.x ? parts[threadIdx.x] : 0u;
+  const uint32_t off = block_incl_scan(before, s_warp);
+  if (threadIdx.x == blockDim.x - 1) s_run = off;
   __syncthreads();
-  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-    const uint32_t v = threadIdx.x >= (unsigned)o ? s_part[threadIdx.x - o] : 0u;
+  int lo, hi;
+  scan_range(a.n_buckets, blockIdx.x, gridDim.x, &lo, &hi);
+  for (int base = lo; base < hi; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const uint32_t v = i < hi ? a.bucket_count[i] : 0u;
+    const uint32_t incl = block_incl_scan(v, s_warp);
+    const uint32_t run = s_run;
+    if (i < hi) a.bucket_count[i] = run + incl - v;
     __syncthreads();
-    s_part[threadIdx.x] += v;
+    if (threadIdx.x == blockDim.x - 1) s_run = run + incl;
     __syncthreads();
   }
-  uint32_t run = s_part[threadIdx.x] - sum;
-  for (int i = lo; i < hi; ++i) {
-    const uint32_t v = a.bucket_count[i];
-    a.bucket_count[i] = run;
-    run += v;
-  }
-  __syncthreads();
-  if (threadIdx.x == blockDim.x - 1) a.bucket_count[n] = run;
-  __syncthreads();
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) a.bucket_count[a.n_buckets] = s_run;
+}
+
+// Per replicate: its first offset (the scatter subtracts it) and its new
+// agent count (the copy and the commit use it).
+__global__ void k_bucket_scan_reps(StepArgs a) {
   for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) {
     const RepDev& R = a.reps[r];
     const uint32_t b0 = a.bucket_count[R.bucket_base];
     const uint32_t b1 = a.bucket_count[R.bucket_base + R.bucket_span];
-    // per replicate: its first offset (the scatter subtracts it) and its new
-    // agent count (the copy and the commit use it)
     a.bucket_count[a.n_buckets + 1 + 2 * r] = b0;
     a.bucket_count[a.n_buckets + 2 + 2 * r] = b1 - b0;
   }
@@ -266,7 +320,10 @@ int resort_launch(const StepArgs& a, const Chunks& ch, int grid, bool force, cud
   if (ch.n <= 0) return 0;
   k_bucket_zero<<<256, 256, 0, s>>>(a);
   k_bucket_count<<<grid, kChunk, 0, s>>>(a, ch);
-  k_bucket_scan<<<1, 1024, 0, s>>>(a);
+  const int nb = std::min(kScanMaxBlocks, std::max(1, (a.n_buckets + 4095) / 4096));
+  k_bucket_scan_parts<<<nb, kScanThreads, 0, s>>>(a);
+  k_bucket_scan_apply<<<nb, kScanThreads, 0, s>>>(a);
+  k_bucket_scan_reps<<<1, 256, 0, s>>>(a);
   k_bucket_scatter<<<grid, kChunk, 0, s>>>(a, ch);
   k_bucket_copy<<<grid, kChunk, 0, s>>>(a, ch);
   k_bucket_commit<<<1, 256, 0, s>>>(a);

@@ -116,7 +116,8 @@ struct StepArgs {
   unsigned long long* dig_cell;  // [dig_cap * n_rep] per-step digests (optional)
   unsigned long long* dig_des;
   int32_t dig_cap;
-  // Morton re-sort scratch: [n_buckets + 1] offsets, then 2 words per replicate
+  // re-sort scratch: [n_buckets + 1] offsets, 2 words per replicate, then the
+  // scan's block sums (up to 1024)
   uint32_t* bucket_count;
   int32_t n_buckets;
   // diagnostics
