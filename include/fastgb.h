@@ -67,7 +67,7 @@ extern "C" {
 #define FAST_CELL_EXIT 2
 
 /* options for fast_set_option */
-#define FAST_OPT_RESORT_PERIOD 1  /* re-sort agents in Morton order every n steps (default 8; 0 never) */
+#define FAST_OPT_RESORT_PERIOD 1  /* re-sort agents in spatial order every n steps (default 8; 0 never) */
 #define FAST_OPT_DIGESTS 2        /* 1: record per-step digests (fast_get_digests)  */
 #define FAST_OPT_LANES_V1 3       /* FP32 planning kernel for v_m=1 (..._V1 + v_m - 1 */
                                   /* for v_m = 1..5): 0 one thread per agent with   */
@@ -77,7 +77,8 @@ extern "C" {
 #define FAST_OPT_BARRIER_NS 10    /* time limit of one device-side wait, ns         */
 #define FAST_OPT_USE_GRAPH 11     /* 1 (default): steps replay a captured CUDA graph */
 #define FAST_OPT_MOVE_BLOCKS 12   /* blocks of the cooperative movement kernel (0: auto) */
-#define FAST_OPT_TILE_SHIFT 13    /* Morton bucket side = 2^shift cells (default 4) */
+#define FAST_OPT_TILE_SHIFT 13    /* re-sort bucket side = 2^shift cells, buckets in */
+                                  /* Hilbert-curve order (default 4)                 */
 #define FAST_OPT_GRAPH_STEPS 14   /* fast_step(n) with 2 <= n <= this (default 512)  */
                                   /* runs the whole n-step loop as one captured     */
                                   /* CUDA graph, kept for later calls at the same   */

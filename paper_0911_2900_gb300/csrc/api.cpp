@@ -257,7 +257,7 @@ void drop_graphs(fast_ctx* c) {
 }
 
 // Work chunks (replicate, first slot) per v_m group and over all replicates;
-// Morton bucket ranges; shared lists sized for all agent slots.
+// re-sort bucket ranges; shared lists sized for all agent slots.
 int rebuild_layout(fast_ctx* c) {
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   drop_graphs(c);
@@ -294,7 +294,7 @@ int rebuild_layout(fast_ctx* c) {
     }
   }
   if (bucket_base > (int64_t)1 << 30)
-    return fail(c, FAST_EINVAL, "too many Morton buckets (%lld); raise the tile shift",
+    return fail(c, FAST_EINVAL, "too many re-sort buckets (%lld); raise the tile shift",
                 (long long)bucket_base);
   for (int v = 1; v <= 5; ++v) {
     std::vector<int32_t> gr, gb;

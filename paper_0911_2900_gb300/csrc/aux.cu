@@ -1,5 +1,5 @@
 // aux.cu -- set-up and bookkeeping kernels: line-of-sight masks, agent
-// placement, Morton re-sort with compaction of agents that left, digests,
+// placement, spatial (Hilbert-order) re-sort with compaction of agents that left, digests,
 // read-back gathers, the reach-union counter used for byte accounting, and
 // the kernels behind the library's self-test entry points.
 #include <algorithm>

@@ -33,7 +33,7 @@ struct alignas(16) MoveEntry {
 struct RepDev {
   int32_t W, H, v, reach, K, mw;    // mw: 64-bit mask words per cell (1 or 2)
   int32_t cap;                      // agent slots allocated
-  int32_t tile_shift;               // Morton buckets are 2^tile_shift square tiles
+  int32_t tile_shift;               // re-sort buckets are 2^tile_shift square tiles
   int32_t tiles_x, tiles_y;         // tiles per row / column
   int32_t bucket_base, bucket_span; // this replicate's range in the bucket arrays
   int32_t claim_tx;                 // 16x16 tiles per row of the claim arrays
