@@ -156,10 +156,26 @@ def test_reach_variants(fg, orc, reach, precision):
 
 
 @pytest.mark.parametrize("lanes", [0, 1, 2, 4, 8])
-def test_lanes_per_agent_variants(fg, orc, lanes):
-    w = wl.config_small_room(W=120, H=90, n=3001, seed=5, v_m=4)
+@pytest.mark.parametrize("v", [1, 4, 5])
+def test_lanes_per_agent_variants(fg, orc, lanes, v):
+    """Every planning variant (tiled, one thread, 2/4/8 lanes per agent) at
+    the smallest reach set, the benchmark's and the largest (two mask words)."""
+    w = wl.config_small_room(W=120, H=90, n=3001, seed=5 + v, v_m=v)
     steps = 25
-    _, (g,) = run_gpu(fg, [w], steps, "fp32_recheck", lanes={4: lanes})
+    _, (g,) = run_gpu(fg, [w], steps, "fp32_recheck", lanes={v: lanes})
+    o = run_oracle(orc, w, steps)
+    assert_same(g, o, steps)
+
+
+@pytest.mark.parametrize("k_S", [0.0, 0.35, 5.0])
+def test_coupling_strengths(fg, orc, k_S):
+    """k_S = 0 (every admissible candidate equally likely: FP32 weights are
+    exactly 1), a weak coupling, and a strong one (weights spread over many
+    binades)."""
+    w0 = wl.config_small_room(W=80, H=70, n=1500, seed=31, v_m=3)
+    w = wl.Workload(w0.name, w0.cell_type, w0.cells, w0.v_m, seed=w0.seed, k_S=k_S)
+    steps = 30
+    _, (g,) = run_gpu(fg, [w], steps, "fp32_recheck")
     o = run_oracle(orc, w, steps)
     assert_same(g, o, steps)
 
