@@ -481,13 +481,6 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
 #pragma unroll
       for (int s = 0; s < 6; ++s)
         if ((need >> s) & 1u) R.cmark[q[s]] = stamp;
-      if (reclaim) {
-        uint32_t* nxt = R.claim[(g + 1u) & 1u];
-        const uint32_t v = claim_of(g + 1u, e.prio);
-#pragma unroll
-        for (int s = 0; s < 6; ++s)
-          if (s <= n) atomicMin(&nxt[q[s]], v);
-      }
       const uint32_t j = append_slot(&s_cnt[1]);
       const MoverLists& dst = j < (uint32_t)kMoveSmemCap ? sm : gl;
       dst.P[j] = e.prio;
@@ -520,7 +513,8 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
   if (tid == 0) atomicMax(&ctl->phase_ns[1], global_ns() - t_start);
   // the cells each waiting agent must keep claiming: the ones it has not
   // held, and the ones it held that another agent lost (claimed too); a
-  // cell only it claims is nobody else's concern for the rest of the step
+  // cell only it claims is nobody else's concern for the rest of the step.
+  // Round 1's claims are made here, on those cells only.
   for (uint32_t k = tid; k < w0; k += blockDim.x) {
     const uint32_t info = ml.IN[k];
     const RepDev& R = a.reps[ml.RF[k] >> 24];
@@ -533,8 +527,15 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
     for (int s = 0; s < 6; ++s)
       if (s <= n && !((need >> s) & 1u) && __ldcg(&R.cmark[q[s]]) == stamp) clm |= 1u << s;
     ml.IN[k] = (info & ~(0x3Fu << MV_CLM)) | (clm << MV_CLM);
+    if (reclaim) {
+      uint32_t* nxt = R.claim[(g + 1u) & 1u];
+      const uint32_t v = claim_of(g + 1u, ml.P[k]);
+#pragma unroll
+      for (int s = 0; s < 6; ++s)
+        if ((clm >> s) & 1u) atomicMin(&nxt[q[s]], v);
+    }
   }
-  __syncthreads();
+  if (!grid_barrier(ctl, nbar)) return;
   uint32_t waiting = __ldcg(&ctl->wait_count[1]);
   if (b == 0 && tid == 0) {
     ctl->round_n[0] = waiting;
