@@ -45,7 +45,7 @@ constexpr int MV_CLM = 23;             // footprint cells the agent must keep cl
                                        // later rounds: those another agent also claims
                                        // (6 bits)
 
-constexpr int kTail = 1024;            // waiting movers one block finishes alone
+constexpr int kTail = 256;             // waiting movers one block finishes alone
 
 // Claim value: an 8-bit round tag g (0..kTags-1; the value falls as g grows)
 // above the 24-bit priority, so a claim of a later round always wins
