@@ -19,9 +19,11 @@
  *   - weight exp(-k_S (S(c) - S(c0))), summed in that order in FP64; the
  *     choice is the smallest k with u*W < C_k, u a 53-bit uniform from
  *     Philox4x32-10 (key = seed, counter = (id, step, 0, 0));
- *   - movement in ascending order of (top 40 bits of Philox(id, step, 1, 0),
- *     id); each agent walks its straight path, stops before a blocked cell,
- *     leaves on entering an exit cell.
+ *   - movement in ascending order of a keyed permutation of the 24-bit ids
+ *     (four Feistel rounds on 12-bit halves, round function
+ *     fmix32(R ^ k_i) & 0xFFF, keys = Philox4x32-10(seed; (0, step, 2, 0)));
+ *     each agent walks its straight path, stops before a blocked cell, leaves
+ *     on entering an exit cell.
  *
  * Conventions for every call:
  *   - cells are row-major indices y*width + x; cell types are 0 free, 1 wall,
