@@ -118,6 +118,16 @@ __device__ __forceinline__ int path_cell_tab(const PathTab* t, int c0, int W, ui
 // Footprints, priorities and first-round outcomes of all movers; agents that
 // stay, or are blocked at their first path cell by an agent that stays, need
 // no work at all.  Also clears the claims at the end of a claim epoch.
+// s * d / L rounded half away from zero (the path cells of Sec. 2), for
+// |d| <= L <= 5 and 1 <= s <= L, given invL = 1/L rounded to nearest.  The
+// quotient is exact in binary for L = 1, 2, 4 and at least 1/10 away from a
+// half for L = 3, 5, so |s * d| * invL + 1/2, rounded once, truncates to the
+// same integer as the exact quotient (checked for every case on the host).
+__device__ __forceinline__ int path_offset(int num, float invL) {
+  const int r = (int)fmaf(fabsf((float)num), invL, 0.5f);
+  return num < 0 ? -r : r;
+}
+
 __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
   // a new claim epoch starts with clean claim and mark arrays (the rounds
   // kernel then starts its tags and stamps from the beginning)
@@ -127,19 +137,24 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
   const int t = a.ctl->t;
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned alive_local = 0, foot_local = 0;
+  int krep = -1;
+  U4 k;
   for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {  // the same chunks for the whole block
     const int rep = ch.rep[c];
     const RepDev& R = a.reps[rep];
     const int end = min(ch.begin[c] + kChunk, a.n_slots[rep]);
     const int slot = ch.begin[c] + threadIdx.x;
     const int cell = slot < end ? R.cell[slot] : -1;
-    // the step's movement-order keys (one Philox block per warp, shared)
-    U4 k;
-    if (lane == 0) k = move_step_keys((uint32_t)t, R.seed_lo, R.seed_hi);
-    k.x = __shfl_sync(0xffffffffu, k.x, 0);
-    k.y = __shfl_sync(0xffffffffu, k.y, 0);
-    k.z = __shfl_sync(0xffffffffu, k.z, 0);
-    k.w = __shfl_sync(0xffffffffu, k.w, 0);
+    // the replicate's movement-order keys for this step (one Philox block
+    // per warp, shared; kept while the block's chunks stay in one replicate)
+    if (rep != krep) {
+      if (lane == 0) k = move_step_keys((uint32_t)t, R.seed_lo, R.seed_hi);
+      k.x = __shfl_sync(0xffffffffu, k.x, 0);
+      k.y = __shfl_sync(0xffffffffu, k.y, 0);
+      k.z = __shfl_sync(0xffffffffu, k.z, 0);
+      k.w = __shfl_sync(0xffffffffu, k.w, 0);
+      krep = rep;
+    }
     bool mover = false;
     MoveEntry e;
     if (cell >= 0) {
@@ -149,12 +164,13 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
       const int x0 = cell % W, y0 = cell / W;
       const int dx = des % W - x0, dy = des / W - y0;
       const int L = max(abs(dx), abs(dy));
+      const float invL = __frcp_rn((float)max(L, 1));
       // all path records first (independent loads), then the scan
       uint32_t pr[6];
 #pragma unroll
       for (int s = 1; s <= 5; ++s)
-        pr[s] = (s <= L) ? R.rec[(y0 + div_half_away(s * dy, L)) * W +
-                                 (x0 + div_half_away(s * dx, L))]
+        pr[s] = (s <= L) ? R.rec[(y0 + path_offset(s * dy, invL)) * W +
+                                 (x0 + path_offset(s * dx, invL))]
                          : REC_STA;
       int fp = 0;
       uint32_t ex = 0;
