@@ -553,6 +553,8 @@ def bench_ours(args):
             "move_rounds_per_step": rounds_per_step,
             "move_last_step": {"waiting_after_round": [int(x) for x in mv_wait[:12]],
                                "round_us": [round(float(x), 2) for x in mv_us[:12]],
+                               "waiting_max_block_after_round":
+                                   [int(x) for x in ctx.last_move_block_max[:12]],
                                "rounds": int(len(mv_wait)),
                                "phases_max_over_blocks": [round(float(x) / 1e3, 2) if i not in (4, 5, 6) else int(x)
                                                           for i, x in enumerate(ctx.last_move_phases)]},

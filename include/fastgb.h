@@ -230,7 +230,9 @@ int fast_phase_times(fast_ctx* ctx, float* ms5);
  * first round's work (ns), the same plus its grid barrier (ns), the second
  * round's work (ns), the first round's claims (ns), movers per block, movers
  * per block still waiting after the first round, the round from which one
- * block finished alone (0: none), 0. */
+ * block finished alone (0: none), 0.  With max_rounds >= 137, t_ns[73 + r]
+ * also receives the most movers still waiting in one block after round r,
+ * for the rounds written. */
 int fast_move_profile(fast_ctx* ctx, int32_t max_rounds, uint32_t* n_wait, uint64_t* t_ns);
 
 /* Runs the FP32 planning of the current state without re-check next to the

@@ -1278,6 +1278,8 @@ int fast_move_profile(fast_ctx* c, int32_t max_rounds, uint32_t* n_wait, uint64_
   if (t_ns && n > 0) t_ns[n] = h.round_ns[n];
   if (t_ns && max_rounds >= 64 + 1 + 8)
     for (int i = 0; i < 8; ++i) t_ns[65 + i] = h.phase_ns[i];
+  if (t_ns && max_rounds >= 64 + 1 + 8 + 64)
+    for (int i = 0; i < n; ++i) t_ns[73 + i] = h.round_bmax[i];
   return h.rounds_last;
 }
 

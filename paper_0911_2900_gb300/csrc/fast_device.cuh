@@ -222,6 +222,27 @@ __device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long
   return __ldcg(p);
 }
 
+// Fire-and-forget reductions on global memory (relaxed, device scope, no
+// value returned), for pointers that point into device global memory.  A
+// plain atomicMin/And/Or/Add through a generic pointer returns the old value
+// to the thread whether or not it is used.
+__device__ __forceinline__ void red_min_u32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.min.u32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v)
+               : "memory");
+}
+__device__ __forceinline__ void red_and_b32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.and.b32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v)
+               : "memory");
+}
+__device__ __forceinline__ void red_or_b32(uint32_t* p, uint32_t v) {
+  asm volatile("red.relaxed.gpu.global.or.b32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v)
+               : "memory");
+}
+__device__ __forceinline__ void red_add_s32(int32_t* p, int32_t v) {
+  asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(v)
+               : "memory");
+}
+
 // Appends to a global list with one atomic per group of converged lanes:
 // returns this lane's slot (called only by the lanes that append).
 __device__ __forceinline__ uint32_t append_slot(uint32_t* counter) {

@@ -93,6 +93,8 @@ struct Ctl {
   unsigned long long round_ns[kRoundLog + 1];
   // per-phase timings of the last step's movement rounds (max over blocks, ns)
   unsigned long long phase_ns[8];
+  // most movers still waiting in one block after each round, last step
+  uint32_t round_bmax[kRoundLog];
 };
 
 struct Chunks {

@@ -357,7 +357,7 @@ __device__ __forceinline__ void commit_move(const StepArgs& a, const RepDev& R, 
     R.cell[slot] = cfin;
   } else {
     R.cell[slot] = -1;
-    atomicAdd(&a.exited[rep], 1);
+    red_add_s32(&a.exited[rep], 1);
   }
 }
 
@@ -373,12 +373,12 @@ __device__ __forceinline__ void commit_first(const StepArgs& a, const RepDev& R,
 #pragma unroll
   for (int s = 1; s <= 5; ++s)
     if (s == fin) cf = c[s];
-  atomicAnd(&R.rec[c[0]], ~(REC_OCC | REC_STA));
+  red_and_b32(&R.rec[c[0]], ~(REC_OCC | REC_STA));
   if (gone) {
     R.cell[slot] = -1;
-    atomicAdd(&a.exited[rep], 1);
+    red_add_s32(&a.exited[rep], 1);
   } else {
-    atomicOr(&R.rec[cf], REC_OCC);
+    red_or_b32(&R.rec[cf], REC_OCC);
     R.cell[slot] = cf;
   }
 }
@@ -417,7 +417,7 @@ __device__ __forceinline__ void claim_list(const StepArgs& a, const PathTab* tab
     uint32_t* cl = R.claim[g & 1u];
 #pragma unroll
     for (int s = 0; s < 6; ++s)
-      if (s <= n_fp) atomicMin(&cl[q[s]], v);
+      if (s <= n_fp) red_min_u32(&cl[q[s]], v);
   }
 }
 
@@ -454,6 +454,9 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
     ctl->round_ns[0] = t_start;
     for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = 0ull;
   }
+  // the per-block maxima are first written after the first grid barrier
+  if (b == 0)
+    for (int i = tid; i < kRoundLog; i += blockDim.x) ctl->round_bmax[i] = 0u;
   __syncthreads();
   bool reclaim = g + 1u < kTags;  // tags left for the next round's claims
 
@@ -468,7 +471,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
     const uint32_t v = claim_of(g, e.prio);
 #pragma unroll
     for (int s = 0; s < 6; ++s)
-      if (s <= n) atomicMin(&cl[q[s]], v);
+      if (s <= n) red_min_u32(&cl[q[s]], v);
   }
   if (tid == 0) atomicMax(&ctl->phase_ns[3], global_ns() - t_start);
   if (!grid_barrier(ctl, nbar)) return;
@@ -524,6 +527,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
     atomicMax(&ctl->phase_ns[0], global_ns() - t_start);
     atomicMax(&ctl->phase_ns[4], (unsigned long long)nb);
     atomicMax(&ctl->phase_ns[5], (unsigned long long)w0);
+    if (w0) atomicMax(&ctl->round_bmax[0], w0);
   }
   if (!grid_barrier(ctl, nbar)) return;
   if (tid == 0) atomicMax(&ctl->phase_ns[1], global_ns() - t_start);
@@ -548,7 +552,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
       const uint32_t v = claim_of(g + 1u, ml.P[k]);
 #pragma unroll
       for (int s = 0; s < 6; ++s)
-        if ((clm >> s) & 1u) atomicMin(&nxt[q[s]], v);
+        if ((clm >> s) & 1u) red_min_u32(&nxt[q[s]], v);
     }
   }
   if (!grid_barrier(ctl, nbar)) return;
@@ -654,7 +658,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
           const uint32_t clm = (info >> MV_CLM) & 0x3Fu;
 #pragma unroll
           for (int s = 0; s < 6; ++s)
-            if ((clm >> s) & 1u) atomicMin(&nxt[q[s]], v);
+            if ((clm >> s) & 1u) red_min_u32(&nxt[q[s]], v);
         }
         if (need != need0) ml.IN[idx] = (info & ~(0x3Fu << MV_NEED)) | (need << MV_NEED);
         lout[append_slot(&s_cnt[out_l])] = idx;
@@ -662,6 +666,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
     }
     __syncthreads();
     if (tid == 0 && r == 1) atomicMax(&ctl->phase_ns[2], global_ns() - t_round);
+    if (tid == 0 && r < kRoundLog && s_cnt[out_l]) atomicMax(&ctl->round_bmax[r], s_cnt[out_l]);
     if (single) {
       __threadfence_block();
       waiting = s_cnt[out_l];
