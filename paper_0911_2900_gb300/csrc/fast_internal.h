@@ -62,9 +62,6 @@ struct Ctl {
   int32_t err;                // first device error (0 = none)
   uint32_t q_count;           // FP64 re-check queue length, this step
   uint32_t act_count[3];      // [2]: movers this step
-  uint32_t wait_count[3];     // movers still waiting after each round (rotation)
-  uint32_t bar_count;         // grid barrier arrivals of the running cooperative launch
-  uint32_t pad_bar;
   int32_t rounds_last;        // movement rounds of the last step
   int32_t rounds_max;
   int32_t resort_period;      // re-sort agents every this many steps (0: never)
@@ -95,6 +92,10 @@ struct Ctl {
   unsigned long long phase_ns[8];
   // most movers still waiting in one block after each round, last step
   uint32_t round_bmax[kRoundLog];
+  // grid barrier words of odd and even barriers, each on a line of its own:
+  // arrivals during the running launch (low half), running sum of the
+  // counts the blocks bring (high half)
+  alignas(128) unsigned long long bar_acc[2][16];
 };
 
 struct Chunks {

@@ -256,42 +256,76 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
 }
 
 // ---------------------------------------------------------------------------
-// Grid-wide barrier for a cooperative launch, with a time limit.  The
-// arrival counter only grows during a launch (it is zero when the launch
-// starts): the n-th barrier of a block completes once n * gridDim.x blocks
-// have arrived.  A block that waits longer than ctl->barrier_ns_limit records
-// the timeout in ctl->err, and every block then leaves the kernel at its next
-// barrier.  `passed` counts the barriers this block has completed.
-__device__ bool grid_barrier(Ctl* ctl, uint32_t& passed) {
+// Grid-wide barrier for a cooperative launch, with a time limit, that also
+// adds up one count over the blocks.  Barriers n = 1, 2, 3, ... of a launch
+// use the words w = ctl->bar_acc[n & 1][0] in turn, zero when the launch
+// starts: every block adds 1 (its arrival) and its count << 32 to w, and
+// the barrier is complete once the low half reaches k * gridDim.x, k the
+// number of barriers so far that used w.  No block can add to w again before
+// every block has passed the barrier in between, so the high half then holds
+// the running sum (mod 2^32) of the counts of w's barriers.  `passed` counts
+// the barriers this block has completed, sum0 and sum1 are the running sums
+// of the two words it saw last; *total receives the sum of this barrier's
+// counts.  The block whose arrival completes the barrier learns it from the
+// atomic itself and does not poll.  A block that waits longer than
+// ctl->barrier_ns_limit records the timeout in ctl->err, and every block then
+// leaves the kernel at its next barrier (the function returns false).
+__device__ bool grid_barrier_sum(Ctl* ctl, uint32_t& passed, uint32_t& sum0, uint32_t& sum1,
+                                 uint32_t count, uint32_t* total) {
   __shared__ int s_ok;
+  __shared__ uint32_t s_total;
   __syncthreads();
   ++passed;
   if (threadIdx.x == 0) {
-    volatile uint32_t* vcount = &ctl->bar_count;
+    const uint32_t p = passed & 1u;
+    unsigned long long* w = &ctl->bar_acc[p][0];
+    volatile unsigned long long* vw = w;
     volatile int* verr = &ctl->err;
-    const uint32_t target = passed * gridDim.x;
-    __threadfence();
-    atomicAdd(&ctl->bar_count, 1u);
     int ok = 1;
-    const unsigned long long t0 = global_ns();
-    const unsigned long long lim = ctl->barrier_ns_limit;
-    while (*vcount < target) {
-      if (*verr != 0) {
-        ok = 0;
-        break;
+    unsigned long long seen = 0ull;
+    if (passed >= 0x7FFFFFFFu / gridDim.x) {
+      // the arrivals would outgrow their half of the word
+      atomicCAS(&ctl->err, 0, kDevErrRounds);
+      ok = 0;
+    } else {
+      const uint32_t target = ((passed + p) >> 1) * gridDim.x;
+      __threadfence();
+      seen = atomicAdd(w, ((unsigned long long)count << 32) | 1ull) +
+             (((unsigned long long)count << 32) | 1ull);
+      const unsigned long long t0 = global_ns();
+      const unsigned long long lim = ctl->barrier_ns_limit;
+      while ((uint32_t)seen != target) {
+        if (*verr != 0) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > lim) {
+          atomicCAS(&ctl->err, 0, kDevErrTimeout);
+          ok = 0;
+          break;
+        }
+        seen = *vw;
       }
-      if (global_ns() - t0 > lim) {
-        atomicCAS(&ctl->err, 0, kDevErrTimeout);
-        ok = 0;
-        break;
-      }
+      __threadfence();
+      if (*verr != 0) ok = 0;
     }
-    __threadfence();
-    if (*verr != 0) ok = 0;
+    const uint32_t run = (uint32_t)(seen >> 32);
+    s_total = run - (p ? sum1 : sum0);
+    if (p)
+      sum1 = run;
+    else
+      sum0 = run;
     s_ok = ok;
   }
   __syncthreads();
+  if (total) *total = s_total;
   return s_ok != 0;
+}
+
+// The barrier without a count (the running sum stays as it is).
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, uint32_t& passed) {
+  uint32_t unused0 = 0u, unused1 = 0u;
+  return grid_barrier_sum(ctl, passed, unused0, unused1, 0u, nullptr);
 }
 
 __device__ __forceinline__ bool round_barrier(Ctl* ctl, bool single, uint32_t& passed) {
@@ -421,6 +455,10 @@ __device__ __forceinline__ void claim_list(const StepArgs& a, const PathTab* tab
   }
 }
 
+// Movers dealt to the blocks of the rounds kernel at a time (one warp's
+// worth of consecutive list entries, so that the entry loads coalesce).
+constexpr uint32_t kSpread = 32;
+
 __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ PathTab tab;
@@ -438,8 +476,18 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
   const uint8_t stamp = (uint8_t)stamp32;
   const uint32_t n0 = min(__ldcg(&ctl->act_count[2]), a.act_cap);
   const uint32_t G = gridDim.x, b = blockIdx.x, tid = threadIdx.x;
-  const uint32_t start = (uint32_t)(((unsigned long long)n0 * b) / G);
-  const uint32_t nb = (uint32_t)(((unsigned long long)n0 * (b + 1)) / G) - start;
+  // the step's movers go to the blocks in turn, kSpread at a time, so that
+  // each block takes movers from all over the list; the block's k-th mover
+  // is entry mover_at(k), and its slice of the global lists is [start, start + nb)
+  const uint32_t nch = (n0 + kSpread - 1) / kSpread;
+  const uint32_t rem = n0 % kSpread, last_owner = nch ? (nch - 1) % G : 0u;
+  uint32_t start = (b * (nch / G) + min(b, nch % G)) * kSpread;
+  uint32_t nb = (b < nch ? (nch - 1 - b) / G + 1 : 0u) * kSpread;
+  if (rem) {
+    if (last_owner < b) start -= kSpread - rem;
+    else if (last_owner == b) nb -= kSpread - rem;
+  }
+  auto mover_at = [&](uint32_t k) { return ((k / kSpread) * G + b) * kSpread + k % kSpread; };
   const MoverLists sm = smem_lists(dsm);  // the block's shared-memory lists
   MoverLists gl;  // the block's slice of global memory
   gl.P = a.mv_prio + start;
@@ -462,7 +510,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
 
   // ---- claims of round 0, straight from the step's list
   for (uint32_t k = tid; k < nb; k += blockDim.x) {
-    const MoveEntry e = a.act[2][start + k];
+    const MoveEntry e = a.act[2][mover_at(k)];
     const RepDev& R = a.reps[e.ref >> 24];
     int c[6], q[6];
     foot_cells(&tab, e.c0, R, e.info, c, q);
@@ -479,7 +527,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
   // ---- round 0: the ones that must wait claim for round 1 and go to the
   // block's lists (shared memory first, global memory beyond its capacity)
   for (uint32_t k = tid; k < nb; k += blockDim.x) {
-    const MoveEntry e = a.act[2][start + k];
+    const MoveEntry e = a.act[2][mover_at(k)];
     const int rep = (int)(e.ref >> 24), slot = (int)(e.ref & 0xFFFFFFu);
     const RepDev& R = a.reps[rep];
     int c[6], q[6];
@@ -522,14 +570,14 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
     }
   MoverLists ml = in_smem ? sm : gl;
   for (uint32_t k = tid; k < w0; k += blockDim.x) ml.L1[k] = k;
-  if (tid == 0 && w0) atomicAdd(&ctl->wait_count[1], w0);
   if (tid == 0) {
     atomicMax(&ctl->phase_ns[0], global_ns() - t_start);
     atomicMax(&ctl->phase_ns[4], (unsigned long long)nb);
     atomicMax(&ctl->phase_ns[5], (unsigned long long)w0);
     if (w0) atomicMax(&ctl->round_bmax[0], w0);
   }
-  if (!grid_barrier(ctl, nbar)) return;
+  uint32_t bsum0 = 0u, bsum1 = 0u, waiting = 0u;  // running sums of the barrier words
+  if (!grid_barrier_sum(ctl, nbar, bsum0, bsum1, w0, &waiting)) return;
   if (tid == 0) atomicMax(&ctl->phase_ns[1], global_ns() - t_start);
   // the cells each waiting agent must keep claiming: the ones it has not
   // held, and the ones it held that another agent lost (claimed too); a
@@ -556,7 +604,6 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
     }
   }
   if (!grid_barrier(ctl, nbar)) return;
-  uint32_t waiting = __ldcg(&ctl->wait_count[1]);
   if (b == 0 && tid == 0) {
     ctl->round_n[0] = waiting;
     ctl->round_ns[1] = global_ns();
@@ -615,7 +662,6 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
     // every agent still waiting checks its claims of tag g, moves if it
     // holds all its cells, else claims with tag g+1
     reclaim = g + 1u < kTags;
-    if (b == 0 && tid == 0) ctl->wait_count[(r + 2) % 3] = 0u;
     const uint32_t n_it = s_cnt[in_l];
     __syncthreads();
     if (tid == 0) s_cnt[out_l] = 0u;
@@ -671,9 +717,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
       __threadfence_block();
       waiting = s_cnt[out_l];
     } else {
-      if (tid == 0 && s_cnt[out_l]) atomicAdd(&ctl->wait_count[(r + 1) % 3], s_cnt[out_l]);
-      if (!grid_barrier(ctl, nbar)) return;
-      waiting = __ldcg(&ctl->wait_count[(r + 1) % 3]);
+      if (!grid_barrier_sum(ctl, nbar, bsum0, bsum1, s_cnt[out_l], &waiting)) return;
     }
     if (b == 0 && tid == 0 && r < kRoundLog) {
       ctl->round_n[r] = waiting;
@@ -722,12 +766,10 @@ int test_barrier_cost_launch(Ctl* ctl, int grid, int block, int iters, cudaStrea
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void reset_step_counters(Ctl* c) {
   c->q_count = 0u;
-  for (int i = 0; i < 3; ++i) {
-    c->act_count[i] = 0u;
-    c->wait_count[i] = 0u;
-  }
+  for (int i = 0; i < 3; ++i) c->act_count[i] = 0u;
   c->tail_count = 0u;
-  c->bar_count = 0u;
+  c->bar_acc[0][0] = 0ull;
+  c->bar_acc[1][0] = 0ull;
 }
 
 __global__ void k_step_begin(StepArgs a) {
