@@ -294,6 +294,13 @@ int fast_selftest_ex2(float lo, float hi, double* max_rel_err);
  * Returns FAST_EINVAL if the grid cannot be co-resident. */
 int fast_selftest_barrier_cost(int32_t blocks, int32_t threads, int32_t iters,
                                double* ns_per_barrier);
+/* Check of the grid barrier's count sums (the movement rounds learn how many
+ * agents still wait from them): a cooperative kernel of `blocks` x `threads`
+ * (all resident) runs `iters` barriers in a row, at barrier i every block
+ * bringing the count (block % 5) + (i % 4); *wrong receives the number of
+ * (block, barrier) pairs whose total differed from the exact sum (0 when the
+ * barrier is right).  Errors as fast_selftest_barrier_cost. */
+int fast_selftest_barrier_sum(int32_t blocks, int32_t threads, int32_t iters, int64_t* wrong);
 /* Runs a cooperative kernel whose grid barrier can never complete, with a
  * wait limit of limit_ns; returns FAST_ETIMEOUT when the wait gave up (the
  * expected outcome) and leaves the CUDA context usable. */

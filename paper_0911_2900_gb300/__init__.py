@@ -105,6 +105,7 @@ EXPORTS = {
     "fast_selftest_ex2": (C.c_int, [C.c_float, C.c_float, C.c_void_p]),
     "fast_selftest_barrier_timeout": (C.c_int, [C.c_int64]),
     "fast_selftest_barrier_cost": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
+    "fast_selftest_barrier_sum": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
 }
 
 
@@ -389,6 +390,15 @@ def selftest_barrier_cost(blocks: int, threads: int, iters: int = 1000) -> float
     rc = load().fast_selftest_barrier_cost(int(blocks), int(threads), int(iters), C.byref(v))
     if rc:
         raise FastError(rc, "fast_selftest_barrier_cost")
+    return v.value
+
+
+def selftest_barrier_sum(blocks: int, threads: int, iters: int = 1000) -> int:
+    """(block, barrier) pairs whose count sum at the grid barrier was wrong."""
+    v = C.c_int64()
+    rc = load().fast_selftest_barrier_sum(int(blocks), int(threads), int(iters), C.byref(v))
+    if rc:
+        raise FastError(rc, "fast_selftest_barrier_sum")
     return v.value
 
 

@@ -1567,6 +1567,26 @@ int fast_selftest_barrier_cost(int32_t blocks, int32_t threads, int32_t iters, d
   return FAST_OK;
 }
 
+int fast_selftest_barrier_sum(int32_t blocks, int32_t threads, int32_t iters, int64_t* wrong) {
+  if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !wrong) return FAST_EINVAL;
+  Ctl* d = nullptr;
+  if (cudaMalloc(&d, sizeof(Ctl)) != cudaSuccess) return FAST_ENOMEM;
+  Ctl h{};
+  h.barrier_ns_limit = 2000000000ull;
+  int rc = FAST_OK;
+  if (cudaMemcpy(d, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess) rc = FAST_ECUDA;
+  if (rc == FAST_OK && test_barrier_sum_launch(d, blocks, threads, iters, 0) != 0) rc = FAST_EINVAL;
+  if (rc == FAST_OK && cudaDeviceSynchronize() != cudaSuccess) rc = FAST_ECUDA;
+  if (rc == FAST_OK && cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = FAST_ECUDA;
+  cudaGetLastError();
+  cudaFree(d);
+  if (rc != FAST_OK) return rc;
+  if (h.err != 0) return FAST_ETIMEOUT;
+  *wrong = (int64_t)h.flips;
+  return FAST_OK;
+}
+
 int fast_selftest_barrier_timeout(int64_t limit_ns) {
   if (limit_ns < 1000 || limit_ns > 10000000000ll) return FAST_EINVAL;
   Ctl* d = nullptr;

@@ -164,6 +164,7 @@ int test_philox_launch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, 
 int test_ex2_launch(float lo, float hi, unsigned long long* out_max_rel_bits, cudaStream_t s);
 int test_barrier_timeout_launch(Ctl* ctl, int grid, cudaStream_t s);
 int test_barrier_cost_launch(Ctl* ctl, int grid, int block, int iters, cudaStream_t s);
+int test_barrier_sum_launch(Ctl* ctl, int grid, int block, int iters, cudaStream_t s);
 int noalloc_plan_launch(const RepDev& R, int32_t cap, int32_t t, int32_t* out, int32_t bound,
                         int sms, cudaStream_t s);
 int noalloc_max_agents();

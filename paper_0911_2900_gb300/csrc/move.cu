@@ -750,6 +750,34 @@ __global__ void __launch_bounds__(1024, 1) k_barrier_cost(Ctl* ctl, int iters) {
   if (blockIdx.x == 0 && threadIdx.x == 0) ctl->round_ns[0] = global_ns() - t0;
 }
 
+// Check of the counting barrier: at barrier i every block brings the count
+// (block % 5) + (i % 4); every block compares each total with the exact sum
+// and counts the differences in ctl->flips.
+__global__ void __launch_bounds__(1024, 1) k_barrier_sum(Ctl* ctl, int iters) {
+  uint32_t nbar = 0, sum0 = 0u, sum1 = 0u;
+  const uint32_t G = gridDim.x;
+  const uint32_t base = (G / 5u) * 10u + (G % 5u) * (G % 5u - 1u) / 2u;  // sum of b % 5
+  for (int i = 0; i < iters; ++i) {
+    uint32_t total = 0u;
+    const uint32_t count = blockIdx.x % 5u + (uint32_t)(i & 3);
+    if (!grid_barrier_sum(ctl, nbar, sum0, sum1, count, &total)) return;
+    if (threadIdx.x == 0 && total != base + G * (uint32_t)(i & 3)) atomicAdd(&ctl->flips, 1ull);
+  }
+}
+
+int test_barrier_sum_launch(Ctl* ctl, int grid, int block, int iters, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_barrier_sum, ctl, iters) == cudaSuccess ? 0 : -1;
+}
+
 int test_barrier_cost_launch(Ctl* ctl, int grid, int block, int iters, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);

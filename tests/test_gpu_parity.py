@@ -117,6 +117,19 @@ def test_bounded_barrier_reports_timeout(fg):
     assert fg.selftest_barrier_timeout(2_000_000) == -5
 
 
+@pytest.mark.parametrize("per_sm", [1, 2])
+def test_grid_barrier_sums_counts_exactly(fg, per_sm):
+    """The movement rounds take the number of agents still waiting from the
+    grid barrier's count sum; on a full grid every block must see the exact
+    total at every barrier (both alternating words, 1000 barriers)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert fg.selftest_barrier_sum(per_sm * sms, 512, 1000) == 0
+    ns = fg.selftest_barrier_cost(per_sm * sms, 512, 1000)
+    assert 0 < ns < 20_000, ns
+
+
 # --------------------------------------------------------------------------- parity
 @pytest.mark.parametrize("precision", ["fp64", "fp32_recheck"])
 def test_room200_2k_v4(fg, orc, precision):
