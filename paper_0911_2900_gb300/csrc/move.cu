@@ -525,19 +525,24 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
   if (!grid_barrier(ctl, nbar)) return;
 
   // ---- round 0: the ones that must wait claim for round 1 and go to the
-  // block's lists (shared memory first, global memory beyond its capacity)
-  for (uint32_t k = tid; k < nb; k += blockDim.x) {
-    const MoveEntry e = a.act[2][mover_at(k)];
-    const int rep = (int)(e.ref >> 24), slot = (int)(e.ref & 0xFFFFFFu);
-    const RepDev& R = a.reps[rep];
+  // block's lists (shared memory first, global memory beyond its capacity).
+  // Two movers per pass: both movers' claim words are in flight together.
+  auto r0_load = [&](const MoveEntry& e, uint32_t* cl) {
+    const RepDev& R = a.reps[e.ref >> 24];
     int c[6], q[6];
     foot_cells(&tab, e.c0, R, e.info, c, q);
     const int n = (int)(e.info & MV_LEN);
     const uint32_t* now = R.claim[g & 1u];
     const uint32_t mine_v = claim_of(g, e.prio);
-    uint32_t cl[6];
 #pragma unroll
     for (int s = 0; s < 6; ++s) cl[s] = (s <= n) ? __ldcg(&now[q[s]]) : mine_v;
+  };
+  auto r0_decide = [&](const MoveEntry& e, const uint32_t* cl) {
+    const int rep = (int)(e.ref >> 24), slot = (int)(e.ref & 0xFFFFFFu);
+    const RepDev& R = a.reps[rep];
+    int c[6], q[6];
+    foot_cells(&tab, e.c0, R, e.info, c, q);
+    const uint32_t mine_v = claim_of(g, e.prio);
     uint32_t need = 0u;
 #pragma unroll
     for (int s = 0; s < 6; ++s) need |= (cl[s] != mine_v) ? (1u << s) : 0u;
@@ -555,6 +560,17 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
       dst.RF[j] = e.ref;
       dst.IN[j] = (e.info & ~(0x3Fu << MV_NEED)) | (need << MV_NEED);
     }
+  };
+  for (uint32_t k = tid; k < nb; k += 2u * blockDim.x) {
+    const bool two = k + blockDim.x < nb;
+    const MoveEntry e1 = a.act[2][mover_at(k)];
+    MoveEntry e2 = e1;
+    if (two) e2 = a.act[2][mover_at(k + blockDim.x)];
+    uint32_t cl1[6], cl2[6];
+    r0_load(e1, cl1);
+    if (two) r0_load(e2, cl2);
+    r0_decide(e1, cl1);
+    if (two) r0_decide(e2, cl2);
   }
   __syncthreads();
   const uint32_t w0 = s_cnt[1];
