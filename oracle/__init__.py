@@ -48,7 +48,7 @@ def build(force: bool = False) -> str:
 class World(C.Structure):
     _fields_ = [("W", C.c_int32), ("H", C.c_int32), ("v", C.c_int32), ("reach", C.c_int32),
                 ("kS", C.c_double), ("seed", C.c_uint64),
-                ("type", C.c_void_p), ("S", C.c_void_p)]
+                ("type", C.c_void_p), ("S", C.c_void_p), ("speed", C.c_void_p)]
 
 
 def _p(a):
@@ -138,14 +138,22 @@ def digest(ids: np.ndarray, vals: np.ndarray) -> int:
 class Sim:
     """One replicate: grid, floor field, agents (id, cell) and occupancy."""
 
-    def __init__(self, cell_type, v, kS=1.2, seed=0, reach=REACH_L2, S=None):
+    def __init__(self, cell_type, v, kS=1.2, seed=0, reach=REACH_L2, S=None, speeds=None):
+        """speeds: optional maximum speed of each agent id (1..5); v is then
+        only a default that no agent uses."""
         self.type = np.ascontiguousarray(cell_type, dtype=np.uint8)
         self.H, self.W = self.type.shape
         if S is None:
             _, _, S = floor_field(self.type)
         self.S = np.ascontiguousarray(S, dtype=np.float64)
+        self.speeds = None
+        if speeds is not None:
+            self.speeds = np.ascontiguousarray(speeds, dtype=np.uint8).copy()
+            if self.speeds.size and (self.speeds.min() < 1 or self.speeds.max() > 5):
+                raise ValueError("speeds must be in 1..5")
         self.world = World(self.W, self.H, v, reach, float(kS), int(seed),
-                           self.type.ctypes.data, self.S.ctypes.data)
+                           self.type.ctypes.data, self.S.ctypes.data,
+                           self.speeds.ctypes.data if self.speeds is not None else None)
         self.occ = np.empty(self.W * self.H, np.int32)
         self.id = np.zeros(0, np.int32)
         self.cell = np.zeros(0, np.int32)
@@ -155,12 +163,15 @@ class Sim:
         n = len(self.cell)
         self.id = (np.arange(n, dtype=np.int32) if ids is None
                    else np.ascontiguousarray(ids, dtype=np.int32).copy())
+        if self.speeds is not None and n and int(self.id.max()) >= len(self.speeds):
+            raise ValueError("speeds does not cover every agent id")
         if lib().orc_build_occ(C.byref(self.world), n, _p(self.cell), _p(self.occ)) != 0:
             raise ValueError("invalid placement (wall/exit/duplicate/outside)")
 
     def plan_agent(self, i: int, t: int):
         """Returns (desired cell, weights[K], u) of agent index i at step t."""
-        K = len(offsets(self.world.v, self.world.reach)[0])
+        v = self.world.v if self.speeds is None else int(self.speeds[self.id[i]])
+        K = len(offsets(v, self.world.reach)[0])
         w = np.zeros(MAXK, np.float64)
         u = C.c_double(0.0)
         d = lib().orc_plan_agent(C.byref(self.world), _p(self.occ), int(self.cell[i]),

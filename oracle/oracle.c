@@ -270,7 +270,9 @@ static int path_clear(const orc_world* w, int x0, int y0, int dx, int dy) {
 }
 
 /* Planning of one agent (Sec. 1: reads only common data; readings R3-R5):
- * candidates are the offsets of the reach set, in canonical order, whose
+ * candidates are the offsets of the reach set of the agent's maximum speed
+ * (w->v, or w->speed[id] when the agents' speeds differ: Sec. 2 notes that
+ * its benchmark gave all agents the same one), in canonical order, whose
  * target is inside the grid, whose path has no wall and whose target is free
  * or is the agent's own cell.  Candidate k gets
  *   d = S[c_k] - S[c0];  x = (-kS) * d;  w_k = exp64(x)
@@ -282,7 +284,8 @@ int32_t orc_plan_agent(const orc_world* w, const int32_t* occ, int32_t cell, int
                        int32_t t, double* w_out, double* u_out) {
   int32_t dx[ORC_MAXK], dy[ORC_MAXK];
   double wk[ORC_MAXK], Ck[ORC_MAXK];
-  int32_t K = orc_offsets(w->v, w->reach, dx, dy);
+  const int32_t v = w->speed ? (int32_t)w->speed[id] : w->v;
+  int32_t K = orc_offsets(v, w->reach, dx, dy);
   const int x0 = cell % w->W, y0 = cell / w->W;
 
   uint32_t ctr[4] = {(uint32_t)id, (uint32_t)t, 0u, 0u};

@@ -40,6 +40,8 @@ typedef struct {
   uint64_t seed;       /* Philox key                                       */
   const uint8_t* type; /* [W*H] ORC_FREE / ORC_WALL / ORC_EXIT               */
   const double* S;     /* [W*H] static floor field (orc_floor_field)        */
+  const uint8_t* speed; /* [ids] maximum speed of each agent id, 1..5, or   */
+                        /* NULL: v for every agent (Sec. 2's benchmark)    */
 } orc_world;
 
 /* Philox4x32-10 (Salmon et al., SC'11), one 128-bit block. */
