@@ -8,10 +8,13 @@ claim is that this gives exactly the sequential result, because an agent's
 walk reads and writes only its footprint (and exits, which stay free).
 
 This file checks the claim on the CPU: a plain Python model of the round
-schedule against the oracle's sequential loop, on random dense scenes with
-walls and exits, for v_m = 1..5.  It also checks that the comparison would
-catch the plausible mistakes in such a schedule (a footprint without the start
-cell, one cut short, the wrong priority order)."""
+schedule, and one with the two filters the GPU kernel applies after the first
+round (only cells not held yet are re-checked; later claims cover only those
+and the held cells another agent lost), against the oracle's sequential loop
+on random dense scenes with walls and exits, for v_m = 1..5.  It also checks
+that the comparison would catch the plausible mistakes in such a schedule (a
+footprint without the start cell, one cut short, the wrong priority order,
+later claims without the held contested cells)."""
 import numpy as np
 import pytest
 
@@ -110,6 +113,94 @@ def round_schedule(t, cells, desired, prio, foot_mode="exact", order="min"):
     return np.array(cell, np.int32), rounds
 
 
+def refined_schedule(t, cells, desired, prio, keep_contested=True):
+    """The same schedule with the two filters the GPU kernel applies after the
+    first round: an agent re-checks only the footprint cells it has not held
+    yet (a cell once held stays held, since its other claimants can only
+    wait), and from the second round on it claims only those cells plus the
+    held ones that another agent lost in the first round (a cell that nobody
+    else claimed is nobody else's concern).  keep_contested=False drops the
+    held contested cells from the later claims (a planted mistake)."""
+    H, W = t.shape
+    flat = t.ravel()
+    n = len(cells)
+    cell = [int(c) for c in cells]
+    stays = {cell[i] for i in range(n) if desired[i] == cell[i]}
+    paths, foot = {}, {}
+    for i in range(n):
+        if desired[i] == cell[i]:
+            continue
+        x0, y0 = cell[i] % W, cell[i] // W
+        dx, dy = int(desired[i]) % W - x0, int(desired[i]) // W - y0
+        p = [(y0 + py) * W + (x0 + px) for px, py in oracle.path(dx, dy)]
+        fp, leaves = [], False
+        for c in p:
+            if flat[c] == WALL or c in stays:
+                break
+            if flat[c] == EXIT:
+                leaves = True
+                break
+            fp.append(c)
+        if not fp and not leaves:
+            continue
+        foot[i] = [cell[i]] + fp
+        paths[i] = p
+    occ = set(cell)
+
+    def walk(i):
+        cur, gone = cell[i], False
+        for c in paths[i]:
+            if flat[c] == WALL or c in occ:
+                break
+            cur = c
+            if flat[c] == EXIT:
+                gone = True
+                break
+        occ.discard(cell[i])
+        if gone:
+            cell[i] = -1
+        else:
+            occ.add(cur)
+            cell[i] = cur
+
+    def owners(claims):
+        own = {}
+        for i, cs in claims.items():
+            for c in cs:
+                if c not in own or prio[i] < prio[own[c]]:
+                    own[c] = i
+        return own
+
+    # first round: every mover claims its whole footprint
+    own = owners(foot)
+    need, contested = {}, set()
+    for i in foot:
+        lost = [c for c in foot[i] if own[c] != i]
+        if lost:
+            need[i] = set(lost)
+            contested.update(lost)
+        else:
+            walk(i)
+    clm = {i: need[i] | ({c for c in foot[i] if c in contested} if keep_contested else set())
+           for i in need}
+    rounds = 1
+    while need:
+        rounds += 1
+        own = owners({i: clm[i] for i in need})
+        done = []
+        for i in need:
+            still = {c for c in need[i] if own.get(c) != i}
+            if not still:
+                done.append(i)
+            else:
+                need[i] = still
+        assert done, "a round without progress"
+        for i in done:
+            walk(i)
+            del need[i]
+    return np.array(cell, np.int32), rounds
+
+
 def sequential(t, cells, desired, v, seed, step):
     sim = oracle.Sim(t, v=v, seed=seed)
     sim.place(cells)
@@ -146,5 +237,23 @@ def test_comparison_catches_a_wrong_schedule(mistake):
         for t, cells, desired, seed, step in scenes(v):
             prio = [oracle.move_priority(seed, i, step) for i in range(len(cells))]
             got, _ = round_schedule(t, cells, desired, prio, **mistake)
+            differ += not np.array_equal(got, sequential(t, cells, desired, v, seed, step))
+    assert differ > 0
+
+
+@pytest.mark.parametrize("v", [1, 2, 3, 4, 5])
+def test_held_and_contested_filters_keep_the_sequential_result(v):
+    for t, cells, desired, seed, step in scenes(v):
+        prio = [oracle.move_priority(seed, i, step) for i in range(len(cells))]
+        got, _ = refined_schedule(t, cells, desired, prio)
+        assert np.array_equal(got, sequential(t, cells, desired, v, seed, step))
+
+
+def test_dropping_the_contested_cells_is_caught():
+    differ = 0
+    for v in (2, 3, 4, 5):
+        for t, cells, desired, seed, step in scenes(v):
+            prio = [oracle.move_priority(seed, i, step) for i in range(len(cells))]
+            got, _ = refined_schedule(t, cells, desired, prio, keep_contested=False)
             differ += not np.array_equal(got, sequential(t, cells, desired, v, seed, step))
     assert differ > 0
