@@ -21,7 +21,7 @@ def assert_valid(w, n=None):
     assert np.all(t[border] != FREE)
     assert not np.any(t[~border] == EXIT)
     assert (t == EXIT).any()
-    # agents: distinct free cells, sorted, inside the grid
+    # agents: distinct free cells inside the grid
     c = w.cells.astype(np.int64)
     assert len(np.unique(c)) == len(c)
     assert np.all((c >= 0) & (c < H * W))
