@@ -161,6 +161,21 @@ int fast_create(fast_ctx** out, int32_t n_replicates, int32_t precision, int32_t
  * long for the 15-bit record fields), FAST_ENOMEM, FAST_ECUDA. */
 int fast_init_grid(fast_ctx* ctx, int32_t replicate, const fast_grid_desc* grid);
 
+/* Gives the agents of one replicate maximum speeds of their own (Sec. 2 runs
+ * its benchmark with one speed for all agents; the model allows one per
+ * agent): speed_by_id: host [n_ids], the speed in 1..5 of every id below
+ * n_ids, copied.  Each agent then plans over the reach set of its own speed;
+ * the movement does not depend on the speed.  Call it after fast_init_grid
+ * and before the replicate's first placement; the speeds hold for every later
+ * placement (an agent whose id has no speed is rejected there) until the next
+ * fast_init_grid.  n_ids = 0 returns to the grid's v_m for every agent.  The
+ * line-of-sight masks of every speed present are built here (one mask array
+ * per speed).  fast_plan_noalloc does not take such replicates.  Errors:
+ * FAST_EINVAL (n_ids outside [0, 2^24], a speed outside 1..5, k_S too large
+ * for the largest speed), FAST_ESTATE (grid not set, or agents already
+ * placed), FAST_ENOMEM, FAST_ECUDA. */
+int fast_set_speeds(fast_ctx* ctx, int32_t replicate, int32_t n_ids, const uint8_t* speed_by_id);
+
 /* Places n agents of one replicate (replacing any previous ones).
  * cells: host [n] distinct free, reachable, non-exit cells (NULL: error);
  * ids: host [n] distinct ids in [0, 2^24); NULL: agent i has id i, and
@@ -169,8 +184,9 @@ int fast_init_grid(fast_ctx* ctx, int32_t replicate, const fast_grid_desc* grid)
  * start_step: index of the next step (all replicates share one step index;
  * resuming a run = placing its read-back state with its step index).
  * The cells and ids are checked on the device.  Errors: FAST_EINVAL (a cell
- * outside the grid, on a wall, unreachable, an exit or taken twice, or an id
- * out of range or repeated; the replicate is then left without agents),
+ * outside the grid, on a wall, unreachable, an exit or taken twice, an id
+ * out of range or repeated, or an id without a speed after fast_set_speeds;
+ * the replicate is then left without agents),
  * FAST_ESTATE (grid not set), FAST_ENOMEM, FAST_ECUDA. */
 int fast_place_agents(fast_ctx* ctx, int32_t replicate, int32_t n, const int32_t* cells,
                       const int32_t* ids, int32_t start_step);

@@ -83,6 +83,7 @@ EXPORTS = {
     "fast_init_grid": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fast_place_agents": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
                                     C.c_int32]),
+    "fast_set_speeds": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p]),
     "fast_step": (C.c_int, [C.c_void_p, C.c_int32]),
     "fast_plan_only": (C.c_int, [C.c_void_p, C.c_int32]),
     "fast_readback": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p,
@@ -218,6 +219,13 @@ class Context:
         H, W = t.shape
         g = GridDesc(W, H, t.ctypes.data, float(k_S), int(v_m), int(seed))
         self._check(self.lib.fast_init_grid(self.h, rep, C.byref(g)), "fast_init_grid")
+
+    def set_speeds(self, rep: int, speed_by_id) -> None:
+        """Maximum speed (1..5) of every agent id of replicate rep; call after
+        init_grid and before the first place.  An empty array returns to the
+        grid's v_m for every agent."""
+        sp = np.ascontiguousarray(speed_by_id, dtype=np.uint8)
+        self._check(self.lib.fast_set_speeds(self.h, rep, len(sp), _ptr(sp)), "fast_set_speeds")
 
     def place(self, rep: int, cells, ids=None, start_step: int = 0):
         c = np.ascontiguousarray(cells, dtype=np.int32)

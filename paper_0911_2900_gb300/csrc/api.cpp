@@ -45,8 +45,14 @@ struct RepHost {
   uint64_t seed = 0;
   int32_t cap = 0;                 // agent slots allocated
   int32_t n = 0;                   // agents placed
+  uint32_t speed_set = 0;          // speeds given per agent (bit s-1: speed s), 0: all v
+  uint8_t* d_speed_by_id = nullptr;  // device copy of the speeds by id
+  int32_t n_speed_ids = 0;
   RepDev d{};                      // device pointers and parameters
 };
+
+// Speeds whose planning launch covers this replicate.
+uint32_t speeds_of(const RepHost& R) { return R.speed_set ? R.speed_set : 1u << (R.v - 1); }
 
 }  // namespace
 
@@ -256,6 +262,34 @@ void drop_graphs(fast_ctx* c) {
   c->multi.clear();
 }
 
+// (Re)allocates a replicate's per-slot arrays for cap >= n slots.
+int realloc_slots(fast_ctx* c, RepHost& R, int32_t n) {
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  int32_t* arrs[] = {R.d.id, R.d.cell, R.d.desired, R.d.id2, R.d.cell2};
+  for (auto p : arrs) dfree(c, p);
+  dfree(c, R.d.prio);
+  dfree(c, R.d.mvinfo);
+  dfree(c, R.d.speed);
+  dfree(c, R.d.speed2);
+  R.d.speed = R.d.speed2 = nullptr;
+  const int32_t cap = std::max(n, std::max(R.cap, 1));
+  if (int e = alloc_into(c, &R.d.id, cap)) return e;
+  if (int e = alloc_into(c, &R.d.cell, cap)) return e;
+  if (int e = alloc_into(c, &R.d.desired, cap)) return e;
+  if (int e = alloc_into(c, &R.d.id2, cap)) return e;
+  if (int e = alloc_into(c, &R.d.cell2, cap)) return e;
+  if (int e = alloc_into(c, &R.d.prio, cap)) return e;
+  if (int e = alloc_into(c, &R.d.mvinfo, cap)) return e;
+  if (R.speed_set) {
+    if (int e = alloc_into(c, &R.d.speed, cap)) return e;
+    if (int e = alloc_into(c, &R.d.speed2, cap)) return e;
+  }
+  R.cap = cap;
+  R.d.cap = cap;
+  c->layout_dirty = true;
+  return FAST_OK;
+}
+
 // Work chunks (replicate, first slot) per v_m group and over all replicates;
 // re-sort bucket ranges; shared lists sized for all agent slots.
 int rebuild_layout(fast_ctx* c) {
@@ -285,7 +319,7 @@ int rebuild_layout(fast_ctx* c) {
     R.d.tiles_y = ty;
     R.d.bucket_base = (int32_t)bucket_base;
     R.d.bucket_span = side * side;
-    bucket_base += (int64_t)side * side;
+    bucket_base += (int64_t)side * side * (R.d.speed ? 5 : 1);  // speed classes
     if (!R.placed) continue;
     total_cap += (uint64_t)R.cap;
     for (int b = 0; b < R.cap; b += kChunk) {
@@ -300,7 +334,7 @@ int rebuild_layout(fast_ctx* c) {
     std::vector<int32_t> gr, gb;
     for (int r = 0; r < c->n_rep; ++r) {
       RepHost& R = c->reps[r];
-      if (!R.grid_set || !R.placed || R.v != v) continue;
+      if (!R.grid_set || !R.placed || !((speeds_of(R) >> (v - 1)) & 1u)) continue;
       for (int b = 0; b < R.cap; b += kChunk) {
         gr.push_back(r);
         gb.push_back(b);
@@ -648,7 +682,14 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   // (re)allocate the per-cell arrays
   dfree(c, R.d.rec);
+  for (int s = 0; s < 5; ++s)
+    if (R.d.mask_v[s] != R.d.mask) dfree(c, R.d.mask_v[s]);
   dfree(c, R.d.mask);
+  for (int s = 0; s < 5; ++s) R.d.mask_v[s] = nullptr;
+  dfree(c, R.d_speed_by_id);
+  R.d_speed_by_id = nullptr;
+  R.n_speed_ids = 0;
+  R.speed_set = 0;
   for (auto& p : R.d.claim) dfree(c, p);
   dfree(c, R.d.cmark);
   R.d.cmark = nullptr;
@@ -678,6 +719,8 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   d.kS = R.kS;
   d.c32 = (float)(-R.kS * kLog2e);
   d.margin = margin_of(R.v, R.K, R.kS);
+  for (int s = 1; s <= 5; ++s) d.margin_v[s - 1] = margin_of(s, reach_count_host(s, c->reach), R.kS);
+  d.mask_v[R.v - 1] = d.mask;
   d.seed_lo = (uint32_t)R.seed;
   d.seed_hi = (uint32_t)(R.seed >> 32);
   CUDA_TRY(c, cudaMemcpyAsync(d.rec, rec.data(), C * 4, cudaMemcpyHostToDevice, c->stream));
@@ -692,6 +735,59 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   if (int e = upload_reps(c)) return e;
   LAUNCH_TRY(c, masks_launch(d, c->d_reps + r, C, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->layout_dirty = true;
+  return FAST_OK;
+}
+
+int fast_set_speeds(fast_ctx* c, int32_t r, int32_t n_ids, const uint8_t* speed_by_id) {
+  if (!c) return FAST_EINVAL;
+  if (c->poisoned) return FAST_ESTATE;
+  if (!rep_ok(c, r)) return fail(c, FAST_EINVAL, "bad replicate index %d", r);
+  RepHost& R = c->reps[r];
+  if (!R.grid_set) return fail(c, FAST_ESTATE, "grid of replicate %d not set", r);
+  if (R.placed)
+    return fail(c, FAST_ESTATE, "replicate %d already has agents: set speeds before placing", r);
+  if (n_ids < 0 || n_ids > (1 << kMaxIdBits))
+    return fail(c, FAST_EINVAL, "id count %d out of range", n_ids);
+  if (n_ids > 0 && !speed_by_id) return fail(c, FAST_EINVAL, "speed_by_id is NULL");
+  uint32_t set = 0;
+  int smax = 0;
+  for (int32_t i = 0; i < n_ids; ++i) {
+    const int v = speed_by_id[i];
+    if (v < 1 || v > 5) return fail(c, FAST_EINVAL, "speed %d of id %d not in 1..5", v, i);
+    set |= 1u << (v - 1);
+    smax = std::max(smax, v);
+  }
+  const double span = R.kS * smax * kSqrt2;
+  if (c->precision != FAST_FP64 && span * kLog2e > 120.0)
+    return fail(c, FAST_EINVAL, "k_S * speed * sqrt2 too large for FP32 weights");
+  if (span > 700.0) return fail(c, FAST_EINVAL, "k_S * speed * sqrt2 too large");
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  dfree(c, R.d_speed_by_id);
+  R.d_speed_by_id = nullptr;
+  R.n_speed_ids = 0;
+  const int64_t C = (int64_t)R.W * R.H;
+  for (int v = 1; v <= 5; ++v) {
+    unsigned long long*& mk = R.d.mask_v[v - 1];
+    const bool want = v == R.v || ((set >> (v - 1)) & 1u);
+    if (!want && mk && mk != R.d.mask) {
+      dfree(c, mk);
+      mk = nullptr;
+    }
+    if (want && !mk) {
+      const int mw = reach_count_host(v, c->reach) > 64 ? 2 : 1;
+      if (int e = alloc_into(c, &mk, (size_t)C * mw)) return e;
+      LAUNCH_TRY(c, masks_speed_launch(c->d_reps + r, C, v, mw, mk, c->stream));
+    }
+  }
+  if (n_ids > 0) {
+    if (int e = alloc_into(c, &R.d_speed_by_id, (size_t)n_ids)) return e;
+    CUDA_TRY(c, cudaMemcpyAsync(R.d_speed_by_id, speed_by_id, (size_t)n_ids,
+                                cudaMemcpyHostToDevice, c->stream));
+    R.n_speed_ids = n_ids;
+  }
+  R.speed_set = set;
+  if (int e = upload_reps(c)) return e;
   c->layout_dirty = true;
   return FAST_OK;
 }
@@ -711,24 +807,8 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   // clear the previous agents' occupancy marks
   if (R.placed && R.cap > 0) LAUNCH_TRY(c, clear_occ_launch(c->d_reps + r, c->d_nslots, r, R.cap, c->stream));
-  if (n > R.cap || !R.placed) {
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    int32_t* arrs[] = {R.d.id, R.d.cell, R.d.desired, R.d.id2, R.d.cell2};
-    for (auto p : arrs) dfree(c, p);
-    dfree(c, R.d.prio);
-    dfree(c, R.d.mvinfo);
-    const int32_t cap = std::max(n, std::max(R.cap, 1));
-    if (int e = alloc_into(c, &R.d.id, cap)) return e;
-    if (int e = alloc_into(c, &R.d.cell, cap)) return e;
-    if (int e = alloc_into(c, &R.d.desired, cap)) return e;
-    if (int e = alloc_into(c, &R.d.id2, cap)) return e;
-    if (int e = alloc_into(c, &R.d.cell2, cap)) return e;
-    if (int e = alloc_into(c, &R.d.prio, cap)) return e;
-    if (int e = alloc_into(c, &R.d.mvinfo, cap)) return e;
-    R.cap = cap;
-    R.d.cap = cap;
-    c->layout_dirty = true;
-  }
+  if (n > R.cap || !R.placed)
+    if (int e = realloc_slots(c, R, n)) return e;
   if (ids && !c->d_id_bits) {
     if (int e = alloc_into(c, &c->d_id_bits, (size_t)1 << (kMaxIdBits - 5))) return e;
     CUDA_TRY(c, cudaMemsetAsync(c->d_id_bits, 0, (size_t)4 << (kMaxIdBits - 5), c->stream));
@@ -751,7 +831,8 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
   // the check and the placement in one pass on the device (slots 0..n-1)
   uint8_t* placed = reinterpret_cast<uint8_t*>(R.d.mvinfo);
   LAUNCH_TRY(c, place_checked_launch(c->d_reps + r, R.d.cell2, ids ? R.d.id2 : nullptr, n, C,
-                                     c->d_id_bits, placed, c->d_place_err, c->stream));
+                                     c->d_id_bits, placed, R.d_speed_by_id, R.n_speed_ids,
+                                     c->d_place_err, c->stream));
   int32_t res[2] = {INT32_MAX, 0};
   CUDA_TRY(c, cudaMemcpyAsync(res, c->d_place_err, 8, cudaMemcpyDeviceToHost, c->stream));
   if (ids)
@@ -769,7 +850,8 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
     if (ids) bad_id = ids[res[0]];
     return fail(c, FAST_EINVAL,
                 "agent %d (id %d): cell %d is outside, not free, unreachable, an exit or taken, "
-                "or the id is outside [0, 2^24) or repeated; the replicate now has no agents",
+                "or the id is outside [0, 2^24), repeated or without a speed; the replicate "
+                "now has no agents",
                 res[0], bad_id, bad_cell);
   }
   R.n = res[1];
@@ -812,24 +894,8 @@ int fast_place_all(fast_ctx* c, const int32_t* counts, const int32_t* cells_by_i
     if (n < 0) continue;
     if (R.placed && R.cap > 0)
       LAUNCH_TRY(c, clear_occ_launch(c->d_reps + r, c->d_nslots, r, R.cap, c->stream));
-    if (n > R.cap || !R.placed) {
-      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-      int32_t* arrs[] = {R.d.id, R.d.cell, R.d.desired, R.d.id2, R.d.cell2};
-      for (auto p : arrs) dfree(c, p);
-      dfree(c, R.d.prio);
-      dfree(c, R.d.mvinfo);
-      const int32_t cap = std::max(n, std::max(R.cap, 1));
-      if (int e = alloc_into(c, &R.d.id, cap)) return e;
-      if (int e = alloc_into(c, &R.d.cell, cap)) return e;
-      if (int e = alloc_into(c, &R.d.desired, cap)) return e;
-      if (int e = alloc_into(c, &R.d.id2, cap)) return e;
-      if (int e = alloc_into(c, &R.d.cell2, cap)) return e;
-      if (int e = alloc_into(c, &R.d.prio, cap)) return e;
-      if (int e = alloc_into(c, &R.d.mvinfo, cap)) return e;
-      R.cap = cap;
-      R.d.cap = cap;
-      c->layout_dirty = true;
-    }
+    if (n > R.cap || !R.placed)
+      if (int e = realloc_slots(c, R, n)) return e;
     R.placed = true;
   }
   if (c->layout_dirty)
@@ -863,8 +929,8 @@ int fast_place_all(fast_ctx* c, const int32_t* counts, const int32_t* cells_by_i
     CUDA_TRY(c, cudaMemsetAsync(R.d.cell, 0xFF, (size_t)R.cap * 4, c->stream));
     LAUNCH_TRY(c, place_checked_launch(c->d_reps + r, c->d_stage + off[r], nullptr, counts[r],
                                        (long long)R.W * R.H, nullptr,
-                                       reinterpret_cast<uint8_t*>(R.d.mvinfo),
-                                       c->d_place_errs + 2 * r, c->stream));
+                                       reinterpret_cast<uint8_t*>(R.d.mvinfo), R.d_speed_by_id,
+                                       R.n_speed_ids, c->d_place_errs + 2 * r, c->stream));
   }
   std::vector<int32_t> slots(c->n_rep), exited(c->n_rep);
   CUDA_TRY(c, cudaMemcpyAsync(res.data(), c->d_place_errs, res.size() * 4, cudaMemcpyDeviceToHost,
@@ -1386,6 +1452,7 @@ int fast_plan_noalloc(fast_ctx* c, int32_t r, int32_t step, int32_t id_bound,
     return fail(c, FAST_EINVAL, "bad replicate, step, id_bound or output pointer");
   RepHost& R = c->reps[r];
   if (!R.placed) return fail(c, FAST_ESTATE, "replicate %d has no agents", r);
+  if (R.speed_set) return fail(c, FAST_EINVAL, "replicate %d has speeds per agent", r);
   if (c->layout_dirty)
     return fail(c, FAST_ESTATE, "layout not built yet: run fast_step or fast_plan_only once first");
   if (R.cap > noalloc_max_agents())

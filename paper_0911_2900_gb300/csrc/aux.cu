@@ -12,7 +12,7 @@ namespace fastgb {
 // Line-of-sight mask of every cell: bit k set when the k-th reach offset lands
 // inside the grid and its straight path crosses no wall (nor any cell that no
 // exit can be reached from).  Static for the lifetime of the grid.
-__global__ void k_masks(const RepDev* rp, int64_t cells) {
+__global__ void k_masks(const RepDev* rp, int64_t cells, int v, int mw, unsigned long long* out) {
   const RepDev R = *rp;
   for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < cells;
        c += (int64_t)gridDim.x * blockDim.x) {
@@ -20,9 +20,9 @@ __global__ void k_masks(const RepDev* rp, int64_t cells) {
     if (!rec_sentinel(R.rec[c])) {
       const int x0 = (int)(c % R.W), y0 = (int)(c / R.W);
       int k = 0;
-      for (int dy = -R.v; dy <= R.v; ++dy)
-        for (int dx = -R.v; dx <= R.v; ++dx) {
-          if (!reach_in(dx, dy, R.v, R.reach)) continue;
+      for (int dy = -v; dy <= v; ++dy)
+        for (int dx = -v; dx <= v; ++dx) {
+          if (!reach_in(dx, dy, v, R.reach)) continue;
           const int tx = x0 + dx, ty = y0 + dy;
           bool ok = tx >= 0 && tx < R.W && ty >= 0 && ty < R.H;
           const int L = max(abs(dx), abs(dy));
@@ -34,15 +34,19 @@ __global__ void k_masks(const RepDev* rp, int64_t cells) {
           ++k;
         }
     }
-    R.mask[c * R.mw] = m[0];
-    if (R.mw > 1) R.mask[c * R.mw + 1] = m[1];
+    out[c * mw] = m[0];
+    if (mw > 1) out[c * mw + 1] = m[1];
   }
 }
 
 int masks_launch(const RepDev& h, RepDev* d, int64_t cells, cudaStream_t s) {
-  (void)h;
+  return masks_speed_launch(d, cells, h.v, h.mw, h.mask, s);
+}
+
+int masks_speed_launch(RepDev* d, int64_t cells, int v, int mw, unsigned long long* out,
+                       cudaStream_t s) {
   const int64_t blocks = (cells + 255) / 256;
-  k_masks<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(d, cells);
+  k_masks<<<(int)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(d, cells, v, mw, out);
   return 0;
 }
 
@@ -73,13 +77,14 @@ int clear_occ_launch(RepDev* d, const int32_t* n_slots, int rep, int cap, cudaSt
 // took, for a roll-back.
 __global__ void k_place_checked(RepDev* rp, const int32_t* cells, const int32_t* ids, int n,
                                 long long n_cells, uint32_t* id_bits, uint8_t* placed,
-                                int32_t* err) {
+                                const uint8_t* speed_by_id, int n_speed_ids, int32_t* err) {
   const RepDev& R = *rp;
   int present = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int c = cells[i];
     const int id = ids ? ids[i] : i;
     placed[i] = 0;
+    if (speed_by_id) R.speed[i] = (id >= 0 && id < n_speed_ids) ? speed_by_id[id] : (uint8_t)1;
     if (!ids && c == -1) {
       R.cell[i] = -1;
       R.id[i] = i;
@@ -87,6 +92,8 @@ __global__ void k_place_checked(RepDev* rp, const int32_t* cells, const int32_t*
       continue;
     }
     bool ok = c >= 0 && (long long)c < n_cells;
+    // with speeds per agent, every placed id needs one
+    ok = ok && (!speed_by_id || (id >= 0 && id < n_speed_ids));
     if (ok) {
       const uint32_t old = atomicOr(&R.rec[c], REC_OCC);
       if (!(old & REC_OCC)) placed[i] = 1;
@@ -119,11 +126,13 @@ __global__ void k_place_rollback(RepDev* rp, const int32_t* cells, int n, const 
 }
 
 int place_checked_launch(RepDev* d, const int32_t* cells, const int32_t* ids, int n,
-                         long long n_cells, uint32_t* id_bits, uint8_t* placed, int32_t* err,
+                         long long n_cells, uint32_t* id_bits, uint8_t* placed,
+                         const uint8_t* speed_by_id, int n_speed_ids, int32_t* err,
                          cudaStream_t s) {
   if (n <= 0) return 0;
   const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
-  k_place_checked<<<grid, 256, 0, s>>>(d, cells, ids, n, n_cells, id_bits, placed, err);
+  k_place_checked<<<grid, 256, 0, s>>>(d, cells, ids, n, n_cells, id_bits, placed, speed_by_id,
+                                       n_speed_ids, err);
   return 0;
 }
 
@@ -163,11 +172,17 @@ __device__ __forceinline__ uint32_t hilbert_index(uint32_t side, uint32_t x, uin
   return d;
 }
 
-__device__ __forceinline__ int bucket_of(const RepDev& R, int cell) {
+// With speeds per agent the buckets come in five speed classes, one after the
+// other, so that the agents of one speed are contiguous (each speed's
+// planning launch then finds its agents together in a warp).
+__device__ __forceinline__ int bucket_classes(const RepDev& R) { return R.speed ? 5 : 1; }
+
+__device__ __forceinline__ int bucket_of(const RepDev& R, int cell, int slot) {
   const int x = cell % R.W, y = cell / R.W;
   uint32_t side = 1;
   while (side * side < (uint32_t)R.bucket_span) side <<= 1;
-  return R.bucket_base +
+  const int cls = R.speed ? (int)R.speed[slot] - 1 : 0;
+  return R.bucket_base + cls * R.bucket_span +
          (int)hilbert_index(side, (uint32_t)(x >> R.tile_shift), (uint32_t)(y >> R.tile_shift));
 }
 
@@ -184,7 +199,7 @@ __global__ void k_bucket_count(StepArgs a, Chunks ch) {
     const int slot = ch.begin[c] + threadIdx.x;
     if (slot >= min(ch.begin[c] + kChunk, a.n_slots[rep])) continue;
     const int cell = R.cell[slot];
-    if (cell >= 0) atomicAdd(&a.bucket_count[bucket_of(R, cell)], 1u);
+    if (cell >= 0) atomicAdd(&a.bucket_count[bucket_of(R, cell, slot)], 1u);
   }
 }
 
@@ -271,7 +286,7 @@ __global__ void k_bucket_scan_reps(StepArgs a) {
   for (int r = threadIdx.x; r < a.n_rep; r += blockDim.x) {
     const RepDev& R = a.reps[r];
     const uint32_t b0 = a.bucket_count[R.bucket_base];
-    const uint32_t b1 = a.bucket_count[R.bucket_base + R.bucket_span];
+    const uint32_t b1 = a.bucket_count[R.bucket_base + R.bucket_span * bucket_classes(R)];
     a.bucket_count[a.n_buckets + 1 + 2 * r] = b0;
     a.bucket_count[a.n_buckets + 2 + 2 * r] = b1 - b0;
   }
@@ -285,10 +300,11 @@ __global__ void k_bucket_scatter(StepArgs a, Chunks ch) {
     if (slot >= min(ch.begin[c] + kChunk, a.n_slots[rep])) continue;
     const int cell = R.cell[slot];
     if (cell < 0) continue;
-    const uint32_t pos = atomicAdd(&a.bucket_count[bucket_of(R, cell)], 1u) -
+    const uint32_t pos = atomicAdd(&a.bucket_count[bucket_of(R, cell, slot)], 1u) -
                          a.bucket_count[a.n_buckets + 1 + 2 * rep];
     R.id2[pos] = R.id[slot];
     R.cell2[pos] = cell;
+    if (R.speed) R.speed2[pos] = R.speed[slot];
     R.mvinfo[pos] = (uint32_t)R.desired[slot];  // movement scratch, free until the next step
   }
 }
@@ -303,6 +319,7 @@ __global__ void k_bucket_copy(StepArgs a, Chunks ch) {
     if (slot < n_new) {
       R.id[slot] = R.id2[slot];
       R.cell[slot] = R.cell2[slot];
+      if (R.speed) R.speed[slot] = R.speed2[slot];
       R.desired[slot] = (int32_t)R.mvinfo[slot];
     } else {
       R.cell[slot] = -1;
@@ -402,12 +419,18 @@ __global__ void k_union_mark(const RepDev* rp, const int32_t* n_slots, int rep, 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int c = R.cell[i];
     if (c < 0) continue;
-    const unsigned long long m0 = R.mask[(size_t)c * R.mw];
-    const unsigned long long m1 = R.mw > 1 ? R.mask[(size_t)c * R.mw + 1] : 0ull;
+    const int v = R.speed ? (int)R.speed[i] : R.v;
+    int K = 0;
+    for (int dy = -v; dy <= v; ++dy)
+      for (int dx = -v; dx <= v; ++dx) K += reach_in(dx, dy, v, R.reach) ? 1 : 0;
+    const int mw = K > 64 ? 2 : 1;
+    const unsigned long long* mk = R.mask_v[v - 1];
+    const unsigned long long m0 = mk[(size_t)c * mw];
+    const unsigned long long m1 = mw > 1 ? mk[(size_t)c * mw + 1] : 0ull;
     int k = 0;
-    for (int dy = -R.v; dy <= R.v; ++dy)
-      for (int dx = -R.v; dx <= R.v; ++dx) {
-        if (!reach_in(dx, dy, R.v, R.reach)) continue;
+    for (int dy = -v; dy <= v; ++dy)
+      for (int dx = -v; dx <= v; ++dx) {
+        if (!reach_in(dx, dy, v, R.reach)) continue;
         const bool bit = k < 64 ? ((m0 >> k) & 1ull) : ((m1 >> (k - 64)) & 1ull);
         if (bit) {
           const int64_t cc = (int64_t)c + (int64_t)dy * R.W + dx;

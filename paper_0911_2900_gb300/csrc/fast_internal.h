@@ -54,6 +54,14 @@ struct RepDev {
   int32_t* cell2;                   // [cap]
   unsigned long long* prio;         // [cap]  movement priority this step
   uint32_t* mvinfo;                 // [cap]  scratch of the re-sort (desired cells)
+  // maximum speed per agent (Sec. 2's benchmark gives every agent the same
+  // one; the model allows one per agent): speed[slot] in 1..5, or nullptr
+  // when every agent has speed v.  Speed classes are re-sorted apart.
+  uint8_t* speed;                   // [cap]
+  uint8_t* speed2;                  // [cap]  re-sort buffer
+  unsigned long long* mask_v[5];    // line-of-sight masks per speed (mask_v[v-1] == mask),
+                                    // K(s) > 64 ? 2 : 1 words per cell; nullptr if unused
+  float margin_v[5];                // margin M of the FP32 decision per speed
 };
 
 // Step-wide control block, resident in device memory.
@@ -145,10 +153,13 @@ int digest_des_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_
 int digest_cell_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s);
 int resort_launch(const StepArgs& a, const Chunks& ch, int grid, bool force, cudaStream_t s);
 int masks_launch(const RepDev& host_rep, RepDev* dev_rep, int64_t cells, cudaStream_t s);
+int masks_speed_launch(RepDev* dev_rep, int64_t cells, int v, int mw, unsigned long long* out,
+                       cudaStream_t s);
 int clear_occ_launch(RepDev* dev_rep, const int32_t* n_slots_dev, int rep, int cap,
                      cudaStream_t s);
 int place_checked_launch(RepDev* dev_rep, const int32_t* cells, const int32_t* ids, int n,
-                         long long n_cells, uint32_t* id_bits, uint8_t* placed, int32_t* err,
+                         long long n_cells, uint32_t* id_bits, uint8_t* placed,
+                         const uint8_t* speed_by_id, int n_speed_ids, int32_t* err,
                          cudaStream_t s);
 int place_rollback_launch(RepDev* dev_rep, const int32_t* cells, int n, const uint8_t* placed,
                           cudaStream_t s);

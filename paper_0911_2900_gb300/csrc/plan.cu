@@ -72,13 +72,15 @@ __global__ void __launch_bounds__(kRcThreads) k_recheck(StepArgs a) {
       RcAgent x;
       x.cell = R.cell[slot];
       x.W = R.W;
-      x.v = R.v;
+      x.v = R.speed ? (int)R.speed[slot] : R.v;  // the agent's own maximum speed
       x.rec = R.rec;
       rec0 = R.rec[x.cell];
       x.S0 = s64_of(rec0);
       x.nks = -R.kS;
-      x.m0 = R.mask[(size_t)x.cell * R.mw];
-      x.m1 = (R.mw > 1) ? R.mask[(size_t)x.cell * R.mw + 1] : 0ull;
+      const unsigned long long* mk = R.mask_v[x.v - 1];
+      const int mw = s_K[x.v - 1] > 64 ? 2 : 1;
+      x.m0 = mk[(size_t)x.cell * mw];
+      x.m1 = (mw > 1) ? mk[(size_t)x.cell * mw + 1] : 0ull;
       x.pad = 0;
       s_ag[tid] = x;
       K = s_K[x.v - 1];

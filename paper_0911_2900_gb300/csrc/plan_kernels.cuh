@@ -30,6 +30,22 @@ __host__ __device__ constexpr int reach_center() {
   return -1;
 }
 
+// With speeds per agent, each speed's launch plans only its own agents.
+template <int V>
+__device__ __forceinline__ bool other_speed(const RepDev& R, int slot) {
+  return R.speed != nullptr && R.speed[slot] != V;
+}
+
+// Line-of-sight mask words of a cell for speed V (K > 64: two words).
+template <int V, int K>
+__device__ __forceinline__ void mask_words(const RepDev& R, int cell, unsigned long long& m0,
+                                           unsigned long long& m1) {
+  constexpr int MW = K > 64 ? 2 : 1;
+  const unsigned long long* mk = R.mask_v[V - 1];
+  m0 = mk[(size_t)cell * MW];
+  m1 = (K > 64) ? mk[(size_t)cell * MW + 1] : 0ull;
+}
+
 // Canonical offsets of one reach set, as cell-index deltas for row length W.
 __device__ __forceinline__ void fill_offsets(int* s_off, int v, int reach, int W) {
   if (threadIdx.x == 0) {
@@ -98,8 +114,8 @@ __device__ __forceinline__ float rec_weight(uint32_t r, float a0m, float b0m, fl
 // settles), the margin test, and the outputs.
 template <int K, int CENTER, bool DIAG, typename WF>
 __device__ __forceinline__ void finish_g1(const StepArgs& a, const RepDev& R, int rep, int slot,
-                                          int cell, float Wt, float u, int norecheck,
-                                          const int* s_dxdy, WF w) {
+                                          int cell, float Wt, float u, float margin,
+                                          int norecheck, const int* s_dxdy, WF w) {
   const float r = __fmul_rn(u, Wt);
   float cacc = 0.f, cprev = 0.f, ck = 0.f;
   int found = -1;
@@ -121,7 +137,7 @@ __device__ __forceinline__ void finish_g1(const StepArgs& a, const RepDev& R, in
       dp[k] = cc / Wt;
     }
   }
-  const float mw = R.margin * Wt;
+  const float mw = margin * Wt;
   const bool ok = (found >= 0) && (r > cprev + mw) && (r < ck - mw);
   const int dd = s_dxdy[found >= 0 ? found : CENTER];
   const int target = cell + ((dd >> 8) - 16) * R.W + ((dd & 0xFF) - 16);
@@ -181,11 +197,11 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
       const int slot = begin + pass * PER_PASS + grp;
       if (slot >= end) continue;
       const int cell = R.cell[slot];
-      if (cell < 0) continue;
+      if (cell < 0 || other_speed<V>(R, slot)) continue;
       const int id = R.id[slot];
       const uint32_t rec0 = rec[cell];
-      const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
-      const unsigned long long m1 = (K > 64) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
+      unsigned long long m0, m1;
+      mask_words<V, K>(R, cell, m0, m1);
       // all candidate records first (independent loads in flight together),
       // then the weights; an inadmissible candidate reads as blocked
       uint32_t rr[Q];
@@ -266,7 +282,7 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
         bool ok;
         if (any) {
           kk = found;
-          const float mw = R.margin * Wt;
+          const float mw = R.margin_v[V - 1] * Wt;
           ok = (r > cprev + mw) && (r < ck - mw);
         } else {
           kk = lastnz;
@@ -311,8 +327,8 @@ __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, 
   constexpr ReachTable<V, REACH> T{};
   const int id = R.id[slot];
   const uint32_t rec0 = p0[0];
-  const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
-  const unsigned long long m1 = (K > 64) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
+  unsigned long long m0, m1;
+  mask_words<V, K>(R, cell, m0, m1);
   uint32_t rr[K];
   // a warp whose agents see every candidate (no wall in sight, inside the
   // grid) skips the per-candidate mask tests
@@ -343,7 +359,7 @@ __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, 
     Wt += wk;
   }
   const float u = plan_uniform24((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
-  finish_g1<K, CENTER, DIAG>(a, R, rep, slot, cell, Wt, u, norecheck, s_dxdy,
+  finish_g1<K, CENTER, DIAG>(a, R, rep, slot, cell, Wt, u, R.margin_v[V - 1], norecheck, s_dxdy,
                              [&](int k) { return w[k]; });
 }
 
@@ -364,7 +380,7 @@ __global__ void __launch_bounds__(256) k_plan_direct(StepArgs a, Chunks ch, int 
     const int slot = ch.begin[c] + threadIdx.x;
     if (slot >= end) continue;
     const int cell = R.cell[slot];
-    if (cell < 0) continue;
+    if (cell < 0 || other_speed<V>(R, slot)) continue;
     plan_one_g1<V, REACH, DIAG, false>(a, R, rep, slot, cell, R.rec + cell, R.W, t, norecheck,
                                        s_dxdy);
   }
@@ -384,7 +400,7 @@ __global__ void __launch_bounds__(256, 2) k_plan_tile(StepArgs a, Chunks ch, int
     const RepDev& R = a.reps[rep];
     const int end = min(ch.begin[c] + kChunk, a.n_slots[rep]);
     const int slot = ch.begin[c] + threadIdx.x;
-    const int cell = slot < end ? R.cell[slot] : -1;
+    const int cell = (slot < end && !other_speed<V>(R, slot)) ? R.cell[slot] : -1;
     const bool live = cell >= 0;
     const int W = R.W;
     int x = 0, y = 0;
@@ -449,8 +465,8 @@ __device__ __forceinline__ int plan_fp64_one(const RepDev& R, const int* s_off, 
   const uint32_t* rec = R.rec;
   const uint32_t rec0 = rec[cell];
   const double S0 = s64_of(rec0);
-  const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
-  const unsigned long long m1 = (K > 64) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
+  unsigned long long m0, m1;
+  mask_words<V, K>(R, cell, m0, m1);
   const double nks = -R.kS;
   double wk[K];
   double W = 0.0;
@@ -502,7 +518,7 @@ __global__ void __launch_bounds__(128) k_plan_fp64(StepArgs a, Chunks ch) {
     const int end = min(begin + kChunk, a.n_slots[rep]);
     for (int slot = begin + threadIdx.x; slot < end; slot += blockDim.x) {
       const int cell = R.cell[slot];
-      if (cell < 0) continue;
+      if (cell < 0 || other_speed<V>(R, slot)) continue;
       const uint32_t rec0 = R.rec[cell];
       const int target = plan_fp64_one<V, REACH>(R, s_off, cell, R.id[slot], t, nullptr);
       R.desired[slot] = target;
@@ -533,7 +549,7 @@ __global__ void __launch_bounds__(128) k_diag_compare(StepArgs a, Chunks ch) {
     const int end = min(begin + kChunk, a.n_slots[rep]);
     for (int slot = begin + threadIdx.x; slot < end; slot += blockDim.x) {
       const int cell = R.cell[slot];
-      if (cell < 0) continue;
+      if (cell < 0 || other_speed<V>(R, slot)) continue;
       double cum[K];
       const int target = plan_fp64_one<V, REACH>(R, s_off, cell, R.id[slot], t, cum);
       const int64_t di = a.diag_base[rep] + slot;
