@@ -52,7 +52,8 @@ KERNEL_SOURCES = {
     "k_plan_tile": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
     "k_plan_fp32": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
     "k_plan_direct": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
-    "k_move_rounds": ["move.cu", "fast_device.cuh", "fast_internal.h"],
+    "k_move_rounds": ["move.cu", "move_common.cuh", "fast_device.cuh", "fast_internal.h"],
+    "k_move_flow": ["move_flow.cu", "move_common.cuh", "fast_device.cuh", "fast_internal.h"],
 }
 
 
@@ -100,7 +101,10 @@ def parse():
                         "if stored there, else tune and store it")
     p.add_argument("--v-m", type=int, default=None,
                    help="v_m of the room and corridors workloads (default 4)")
-    p.add_argument("--fp64-steps", type=int, default=3)
+    p.add_argument("--fp64-steps", type=int, default=None,
+                   help="steps of the all-FP64 form timed (default: --steps)")
+    p.add_argument("--move-schedule", default="flow", choices=["flow", "rounds"],
+                   help="GPU schedule of the sequential movement (same results)")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -225,10 +229,19 @@ def max_over_ranks(x, world, op="max"):
 
 
 def plan_bytes(n_agents, union_cells, mask_words):
-    """Algorithmic bytes of one planning pass: per agent id, cell, mask,
-    desired write and own-record write; per cell of the reach union one
-    4-byte record."""
+    """Algorithmic bytes of one planning pass as this library lays the data
+    out: per agent id, cell, mask, desired write and own-record write; per
+    cell of the reach union one 4-byte record (floor field and occupancy
+    packed in one word)."""
     return n_agents * (4 + 4 + 8 * mask_words + 4 + 4) + union_cells * 4
+
+
+def plan_bytes_separate_arrays(n_agents, union_cells, rechecked, K):
+    """The same pass counted with the floor field and the occupancy as two
+    separate 4-byte arrays and a 16-byte mask per agent, plus the FP64 floor
+    field of the re-checked agents' candidates: per agent id, cell, mask and
+    desired (28 B), per union cell 8 B, per re-checked agent K doubles."""
+    return n_agents * 28 + union_cells * 8 + rechecked * K * 8
 
 
 def move_bytes(movers, footprint_cells):
@@ -331,6 +344,9 @@ def bench_ours(args):
     n_rep = len(works)
     n0 = [int(len(w.cells)) for w in works]
     mask_words = [1 if w.v_m <= 4 else 2 for w in works]
+    fp64_steps = args.fp64_steps if args.fp64_steps is not None else args.steps
+    flow = args.move_schedule == "flow"
+    move_kernel = "k_move_flow" if flow else "k_move_rounds"
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     loop_graph = args.workload == "batch"
@@ -365,11 +381,15 @@ def bench_ours(args):
     def union_bytes(ctx, alive):
         return sum(plan_bytes(alive[r], ctx.reach_union(r), mask_words[r]) for r in range(n_rep))
 
+    def union_cells(ctx):
+        return [ctx.reach_union(r) for r in range(n_rep)]
+
     def alive_now(ctx):
         return [ctx.readback(r, 0)[2]["alive"] for r in range(n_rep)]
 
     def make_ctx(precision):
         ctx = fg.Context(n_rep, precision)
+        ctx.set_option("move_schedule", 1 if flow else 0)
         for r, w in enumerate(works):
             ctx.init_grid(r, w.cell_type, w.k_S, w.v_m, w.seed)
             ctx.place(r, w.cells)
@@ -391,6 +411,7 @@ def bench_ours(args):
     torch.cuda.synchronize()
     al0 = alive_now(ctx)
     b0 = union_bytes(ctx, al0)
+    u0 = union_cells(ctx)
     _, _, st0 = ctx.readback(0, 0)
     gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) \
         if os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
@@ -409,8 +430,11 @@ def bench_ours(args):
     clk = clocks.stop()
     _, _, st1 = ctx.readback(0, 0)
     mv_wait, mv_us = ctx.move_profile()
+    ctx_phases = list(ctx.last_move_phases)
+    ctx_block_max = list(ctx.last_move_block_max)
     al1 = alive_now(ctx)
     b1 = union_bytes(ctx, al1)
+    u1 = union_cells(ctx)
     agent_steps = st1["agent_steps"] - st0["agent_steps"]
     launches = st1["kernel_launches"] - st0["kernel_launches"]
     movers = (st1["movers"] - st0["movers"]) / args.steps
@@ -422,7 +446,7 @@ def bench_ours(args):
         # phase breakdown, and the FP32 form timed like the FP64 form below
         # (per step, L2 flushed), from a few extra steps not in the value
         _, _, sp0 = ctx.readback(0, 0)
-        ms32, phases = timed_steps(ctx, max(args.fp64_steps, min(4, args.steps)))
+        ms32, phases = timed_steps(ctx, max(fp64_steps, min(4, args.steps)))
         _, _, sp1 = ctx.readback(0, 0)
         step32_value = (sp1["agent_steps"] - sp0["agent_steps"]) / (sum(ms32) / 1e3)
     else:
@@ -441,6 +465,12 @@ def bench_ours(args):
     bytes_plan = 0.5 * (b0 + b1)
     peak, peak_kind = measured_peaks()
     achieved = bytes_plan / (statistics.mean(plan_ms) / 1e3) / 1e9
+    K_by_v = {1: 5, 2: 13, 3: 29, 4: 49, 5: 81}
+    bytes_plan_sep = sum(plan_bytes_separate_arrays(
+        0.5 * (al0[r] + al1[r]), 0.5 * (u0[r] + u1[r]),
+        rechecked * (al0[r] + al1[r]) / max(1, sum(al0) + sum(al1)), K_by_v[works[r].v_m])
+        for r in range(n_rep))
+    achieved_sep = bytes_plan_sep / (statistics.mean(plan_ms) / 1e3) / 1e9
     bytes_move = move_bytes(movers, foot)
     achieved_move = bytes_move / (statistics.mean(rounds_ms) / 1e3) / 1e9
 
@@ -458,7 +488,7 @@ def bench_ours(args):
     ctx64.step(1)
     torch.cuda.synchronize()
     _, _, s640 = ctx64.readback(0, 0)
-    ms64, ph64 = timed_steps(ctx64, args.fp64_steps)
+    ms64, ph64 = timed_steps(ctx64, fp64_steps)
     _, _, s641 = ctx64.readback(0, 0)
     as64 = s641["agent_steps"] - s640["agent_steps"]
     fp64_value = max_over_ranks(as64, world, "sum") / max_over_ranks(sum(ms64) / 1e3, world)
@@ -513,6 +543,20 @@ def bench_ours(args):
         cpu = {"value": c["value"], "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": c["sample"], "choices_per_s": c["choices_per_s"]}
 
+    ph = ctx_phases
+    if flow:
+        move_last = {"pass1_us": round(ph[0] / 1e3, 2), "barrier_done_us": round(ph[1] / 1e3, 2),
+                     "pass2_us": round(ph[2] / 1e3, 2), "first_rounds_us": round(ph[3] / 1e3, 2),
+                     "movers_per_block_max": int(ph[4]),
+                     "waiting_after_pass2_block_max": int(ph[5]), "overflow_waves": int(ph[6]),
+                     "block_rounds_max": int(ph[7]), "times": "max over blocks, from kernel start"}
+    else:
+        move_last = {"waiting_after_round": [int(x) for x in mv_wait[:12]],
+                     "round_us": [round(float(x), 2) for x in mv_us[:12]],
+                     "waiting_max_block_after_round": [int(x) for x in ctx_block_max[:12]],
+                     "rounds": int(len(mv_wait)),
+                     "phases_max_over_blocks": [round(float(x) / 1e3, 2) if i not in (4, 5, 6)
+                                                else int(x) for i, x in enumerate(ph)]}
     if rank == 0:
         cfg = workload_config(works, args.workload)
         cfg.update({"precision": "fp32 weights + fp64 re-check",
@@ -539,7 +583,7 @@ def bench_ours(args):
             "config": cfg,
             "choices_per_s": choices,
             "fp64_form": {"value": fp64_value, "choices_per_s": fp64_choices, "unit": UNIT,
-                          "steps": args.fp64_steps,
+                          "steps": fp64_steps,
                           "timing": "per step, L2 flushed before each"},
             "phase_ms": {"plan": statistics.mean(plan_ms), "recheck": statistics.mean(recheck_ms),
                          "move_prep": statistics.mean(prep_ms),
@@ -550,24 +594,22 @@ def bench_ours(args):
             "movers_per_step": movers,
             "rechecked_per_step": rechecked,
             "tile_fallback_warps_per_step": fallbacks,
+            "move_schedule": args.move_schedule,
             "move_rounds_per_step": rounds_per_step,
-            "move_last_step": {"waiting_after_round": [int(x) for x in mv_wait[:12]],
-                               "round_us": [round(float(x), 2) for x in mv_us[:12]],
-                               "waiting_max_block_after_round":
-                                   [int(x) for x in ctx.last_move_block_max[:12]],
-                               "rounds": int(len(mv_wait)),
-                               "phases_max_over_blocks": [round(float(x) / 1e3, 2) if i not in (4, 5, 6) else int(x)
-                                                          for i, x in enumerate(ctx.last_move_phases)]},
-            "roofline": {"bound": "hbm", "kernel": "k_move_rounds", "achieved": achieved_move,
+            "move_last_step": move_last,
+            "roofline": {"bound": "hbm", "kernel": move_kernel, "achieved": achieved_move,
                          "peak": peak, "unit": "GB/s", "frac": achieved_move / peak,
-                         "traffic": measured_traffic("k_move_rounds", label),
+                         "traffic": measured_traffic(move_kernel, label),
                          "peak_kind": peak_kind, "bytes_per_launch": bytes_move,
-                         "note": "dominant kernel; bound by the number of rounds and "
-                                 "dependent scattered memory operations, not bandwidth"},
+                         "note": "dominant kernel; bound by the latency of dependent "
+                                 "scattered memory operations along priority chains, not "
+                                 "bandwidth"},
             "roofline_plan": {"bound": "hbm", "kernel": plan_kernel, "achieved": achieved,
                               "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                               "traffic": measured_traffic(plan_kernel, label),
-                              "peak_kind": peak_kind, "bytes_per_launch": bytes_plan},
+                              "peak_kind": peak_kind, "bytes_per_launch": bytes_plan,
+                              "bytes_per_launch_separate_arrays": bytes_plan_sep,
+                              "frac_separate_arrays": achieved_sep / peak},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),

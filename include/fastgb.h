@@ -92,6 +92,19 @@ extern "C" {
 #define FAST_OPT_CLAIM_TAG 16     /* clears the claims and sets the next step's     */
                                   /* first claim tag, 0..254: a test hook for the   */
                                   /* clean-ups; results do not depend on it         */
+#define FAST_OPT_MOVE_SCHEDULE 17 /* how the sequential movement runs on the GPU    */
+                                  /* (same result either way): 1 (default) a        */
+                                  /* dataflow over the conflict graph, one grid     */
+                                  /* barrier per step; 0 rounds of claims, one grid */
+                                  /* barrier per round                              */
+#define FAST_OPT_FLOW_LIST_CAP 18 /* dataflow schedule: released movers a block     */
+                                  /* keeps in shared memory per round, 1..8192     */
+                                  /* (0: 8192); more spill into a global list that  */
+                                  /* all blocks share after a grid barrier.  A test */
+                                  /* hook; results do not depend on it              */
+#define FAST_OPT_FLOW_TAG 19      /* dataflow schedule: tag of the last pass's list */
+                                  /* heads, 0..0xFFFFFF00 (there the heads are      */
+                                  /* cleared and the tags restart): a test hook    */
 
 typedef struct fast_ctx fast_ctx;
 
@@ -107,6 +120,19 @@ typedef struct {
   double k_S;               /* coupling to the static floor field (>= 0)     */
   int32_t v_m;              /* maximum speed, 1..5 cells per step            */
   uint64_t seed;            /* Philox key of this replicate                  */
+  const double* static_field; /* host [width*height] or NULL, borrowed: the    */
+                            /* caller's static floor field S per cell instead */
+                            /* of the library's 8-neighbour distance to the   */
+                            /* exits.  The library keeps S exactly as step    */
+                            /* counts (a, b), S = a + b*sqrt(2), so every     */
+                            /* value must be of that form as the FP64 rule    */
+                            /* rounds it, fl(a + fl(b*sqrt2)), integers       */
+                            /* 0 <= a, b <= 32766 (any field made of          */
+                            /* orthogonal and diagonal steps is); exit cells  */
+                            /* need 0 and no other cell may be 0; +inf marks  */
+                            /* a free cell treated as a wall (no exit         */
+                            /* reachable); values of wall cells are ignored.  */
+                            /* Another field is refused with FAST_EINVAL.     */
 } fast_grid_desc;
 
 typedef struct {
@@ -157,8 +183,11 @@ int fast_create(fast_ctx** out, int32_t n_replicates, int32_t precision, int32_t
 /* Sets the grid of one replicate: validates the cell types, computes the
  * exact floor field on the host, uploads cell records and line-of-sight
  * masks.  Every free cell that no exit can be reached from is treated as a
- * wall.  Errors: FAST_EINVAL (types, size, v_m, k_S, no exit, distance too
- * long for the 15-bit record fields), FAST_ENOMEM, FAST_ECUDA. */
+ * wall.  With grid->static_field the caller's field replaces the computed
+ * one (its +inf cells are the walls so added).  Errors: FAST_EINVAL (types,
+ * size, v_m, k_S, no exit, distance too long for the 15-bit record fields, a
+ * static_field value that is not of the form above), FAST_ENOMEM,
+ * FAST_ECUDA. */
 int fast_init_grid(fast_ctx* ctx, int32_t replicate, const fast_grid_desc* grid);
 
 /* Gives the agents of one replicate maximum speeds of their own (Sec. 2 runs
@@ -266,8 +295,11 @@ int fast_reach_union(fast_ctx* ctx, int32_t replicate, int64_t* cells);
  * is all held by another allocator).  It writes, for each agent of the
  * replicate present in the context with id < id_bound, the desired cell of
  * step `step` into desired_by_id_dev[id] (a device buffer the caller owns;
- * other entries are left as they are), computed exactly like a planning pass
- * of the context (FP32 weights, FP64 re-check inside the margin).  The
+ * other entries are left as they are).  It always plans with FP32 weights
+ * and the FP64 re-check inside the margin, whatever precision the context
+ * has, so its output is the FP64 rule's choice (equal to a planning pass of a
+ * FAST_FP64 or FAST_FP32_RECHECK context; a FAST_FP32_NORECHECK context's own
+ * planning may differ near a boundary).  The
  * context's state is read, never changed, and the call only queues work on
  * the context's stream.  Its scratch is one fixed array of 4 MiB + 256 bytes
  * inside the library, held on every device that loads the library until the
@@ -293,6 +325,20 @@ int fast_plan_noalloc(fast_ctx* ctx, int32_t replicate, int32_t step, int32_t id
  * the times.  With precision FAST_FP64 nothing is tuned.  Errors:
  * FAST_EINVAL (trials not in 1..1000), FAST_ESTATE (no agents), FAST_ECUDA. */
 int fast_autotune(fast_ctx* ctx, int32_t trials, fast_tune_report* out);
+
+/* Host only (no GPU, no context): the static floor field fast_init_grid
+ * would use for this grid.  With static_field NULL, the library's field (the
+ * exact 8-neighbour distance to the exits, costs 1 and sqrt(2)); else the
+ * caller's field checked and decomposed as fast_grid_desc describes.  Writes
+ * (each pointer may be NULL; host arrays [width*height]) S_out: S per cell as
+ * the FP64 rule rounds it, fl(a + fl(b*sqrt2)), +inf for walls and cells no
+ * exit is reached from; a_out, b_out: the step counts (-1 there).  For
+ * editing a field before passing it back through fast_grid_desc.  Errors:
+ * FAST_EINVAL (size, a cell type > 2, a static_field value of the wrong
+ * form), with *bad_cell (may be NULL) the first offending cell, else -1. */
+int fast_floor_field(int32_t width, int32_t height, const uint8_t* cell_type,
+                     const double* static_field, double* S_out, int32_t* a_out, int32_t* b_out,
+                     int64_t* bad_cell);
 
 int fast_set_option(fast_ctx* ctx, int32_t option, int64_t value);
 const char* fast_last_error(const fast_ctx* ctx);

@@ -333,29 +333,38 @@ int32_t orc_plan_agent(const orc_world* w, const int32_t* occ, int32_t cell, int
   return (y0 + dy[chosen]) * w->W + (x0 + dx[chosen]);
 }
 
-/* All agents.  With threads > 1 the loop is partitioned as in Sec. 2:
- * blocksize = max(min(n / cores, 32767), 1), dynamic schedule. */
+/* Agents per chunk of the timed planning loop (Sec. 2 gives the rule): about
+ * an equal share per thread, capped at 32767 agents, at least one. */
+static int32_t orc_chunk_agents(int32_t n, int32_t threads) {
+  const int32_t share = n / threads;
+  return share < 1 ? 1 : (share > 32767 ? 32767 : share);
+}
+
+/* All agents.  With threads > 1 (the timed CPU baseline) the threads take
+ * chunks of consecutive agents on demand, each from a shared counter, until
+ * none is left; the result does not depend on who plans which agent (every
+ * draw is keyed by the agent's id and the step). */
 void orc_plan_all(const orc_world* w, const int32_t* occ, int32_t n, const int32_t* id,
                   const int32_t* cell, int32_t t, int32_t* desired, int32_t threads) {
-  if (threads <= 1) {
-    for (int32_t i = 0; i < n; ++i)
-      desired[i] = cell[i] < 0 ? -1 : orc_plan_agent(w, occ, cell[i], id[i], t, 0, 0);
-    return;
-  }
+  int32_t next = 0;
+  const int32_t chunk = threads > 1 ? orc_chunk_agents(n, threads) : (n > 0 ? n : 1);
 #ifdef _OPENMP
-  int32_t blocksize = n / threads;
-  if (blocksize > 32767) blocksize = 32767;
-  if (blocksize < 1) blocksize = 1;
-#pragma omp parallel num_threads(threads)
-  {
-#pragma omp for schedule(dynamic, blocksize)
-    for (int32_t i = 0; i < n; ++i)
+#pragma omp parallel num_threads(threads > 1 ? threads : 1)
+#endif
+  for (;;) {
+    int32_t begin;
+#ifdef _OPENMP
+#pragma omp atomic capture
+#endif
+    {
+      begin = next;
+      next += chunk;
+    }
+    if (begin >= n) break;
+    const int32_t end = n - begin < chunk ? n : begin + chunk;
+    for (int32_t i = begin; i < end; ++i)
       desired[i] = cell[i] < 0 ? -1 : orc_plan_agent(w, occ, cell[i], id[i], t, 0, 0);
   }
-#else
-  for (int32_t i = 0; i < n; ++i)
-    desired[i] = cell[i] < 0 ? -1 : orc_plan_agent(w, occ, cell[i], id[i], t, 0, 0);
-#endif
 }
 
 /* ------------------------------------------------------------------------- */

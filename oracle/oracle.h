@@ -13,12 +13,12 @@
  *           agent, so that no two agents ever share a cell;
  *   Sec. 2: k_S = 1.2, k_other = 0, one maximum speed v_m for all agents,
  *           one step = one simulated second; the planning loop is the only
- *           parallel region (OpenMP, dynamic schedule with
- *           blocksize = max(min(N / cores, 32767), 1)).
- * The paper does not restate the model's rules; the readings this oracle
+ *           parallel region, its agents dealt to the cores in chunks taken
+ *           on demand.
+ * The paper does not restate the model's rules; each reading this oracle
  * implements (reach set, line of sight, weight, sampling rule, random numbers,
- * path rasterisation, movement order, exits) are listed in the design doc and in
- * the comments of oracle.c, each at the function that implements it.
+ * path rasterisation, movement order, exits) is stated in the comment of the
+ * function of oracle.c that implements it.
  */
 #ifndef FAST_ORACLE_H
 #define FAST_ORACLE_H

@@ -23,7 +23,8 @@ PRECISION = {"fp64": 0, "fp32_recheck": 1, "fp32_norecheck": 2}
 REACH = {"l2": 0, "l2p": 1, "linf": 2}
 OPT = {"resort_period": 1, "digests": 2, "lanes_v1": 3, "lanes_v2": 4, "lanes_v3": 5,
        "lanes_v4": 6, "lanes_v5": 7, "barrier_ns": 10, "use_graph": 11, "move_blocks": 12,
-       "tile_shift": 13, "graph_steps": 14, "claim_reserve": 15, "claim_tag": 16}
+       "tile_shift": 13, "graph_steps": 14, "claim_reserve": 15, "claim_tag": 16,
+       "move_schedule": 17, "flow_list_cap": 18, "flow_tag": 19}
 ERRORS = {0: "FAST_OK", -1: "FAST_EINVAL", -2: "FAST_ESTATE", -3: "FAST_ENOMEM",
           -4: "FAST_ECUDA", -5: "FAST_ETIMEOUT"}
 
@@ -36,7 +37,8 @@ class FastError(RuntimeError):
 
 class GridDesc(C.Structure):
     _fields_ = [("width", C.c_int32), ("height", C.c_int32), ("cell_type", C.c_void_p),
-                ("k_S", C.c_double), ("v_m", C.c_int32), ("seed", C.c_uint64)]
+                ("k_S", C.c_double), ("v_m", C.c_int32), ("seed", C.c_uint64),
+                ("static_field", C.c_void_p)]
 
 
 class Stats(C.Structure):
@@ -94,6 +96,8 @@ EXPORTS = {
     "fast_move_profile": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "fast_reach_union": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fast_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "fast_floor_field": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p]),
     "fast_plan_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
     "fast_autotune": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fast_place_all": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]),
@@ -214,10 +218,19 @@ class Context:
 
     # -- API ---------------------------------------------------------------------
     def init_grid(self, rep: int, cell_type: np.ndarray, k_S: float = 1.2, v_m: int = 4,
-                  seed: int = 0):
+                  seed: int = 0, static_field=None):
+        """static_field: optional float64 array shaped like cell_type, the
+        caller's floor field (see fast_grid_desc); None: the library computes
+        the 8-neighbour distance to the exits."""
         t = np.ascontiguousarray(cell_type, dtype=np.uint8)
         H, W = t.shape
-        g = GridDesc(W, H, t.ctypes.data, float(k_S), int(v_m), int(seed))
+        S = None
+        if static_field is not None:
+            S = np.ascontiguousarray(static_field, dtype=np.float64)
+            if S.shape != t.shape:
+                raise ValueError("static_field must have the shape of cell_type")
+        g = GridDesc(W, H, t.ctypes.data, float(k_S), int(v_m), int(seed),
+                     S.ctypes.data if S is not None else None)
         self._check(self.lib.fast_init_grid(self.h, rep, C.byref(g)), "fast_init_grid")
 
     def set_speeds(self, rep: int, speed_by_id) -> None:
@@ -311,8 +324,20 @@ class Context:
         return v.value
 
     def plan_noalloc(self, rep: int, step: int, out_by_id) -> None:
-        """Allocation-free planning pass into `out_by_id` (a CUDA int32 tensor,
-        indexed by agent id); queued on the context's stream."""
+        """Allocation-free planning pass into `out_by_id` (a contiguous int32
+        tensor on this context's CUDA device, indexed by agent id); queued on
+        the context's stream.  The library writes through the raw pointer and
+        cannot check what it points to, so the tensor is checked here."""
+        import torch
+
+        if not isinstance(out_by_id, torch.Tensor):
+            raise ValueError("out_by_id must be a torch tensor")
+        if out_by_id.dtype != torch.int32:
+            raise ValueError(f"out_by_id must be int32, not {out_by_id.dtype}")
+        if not out_by_id.is_contiguous():
+            raise ValueError("out_by_id must be contiguous")
+        if not out_by_id.is_cuda or out_by_id.device != torch.device(self.device):
+            raise ValueError(f"out_by_id must be on {self.device}, not {out_by_id.device}")
         self._check(self.lib.fast_plan_noalloc(self.h, rep, int(step), int(out_by_id.numel()),
                                                C.c_void_p(out_by_id.data_ptr())),
                     "fast_plan_noalloc")
@@ -359,6 +384,30 @@ class Context:
 
     def set_option(self, name: str, value: int):
         self._check(self.lib.fast_set_option(self.h, OPT[name], int(value)), "fast_set_option")
+
+
+def floor_field(cell_type, static_field=None):
+    """The static floor field fast_init_grid uses for this grid (host only,
+    no GPU): (S, a, b) shaped like cell_type, S = fl(a + fl(b*sqrt2)), +inf
+    and -1 at walls and cells no exit is reached from.  With static_field,
+    the caller's field checked and decomposed into its step counts (a
+    FastError names the first cell of the wrong form)."""
+    t = np.ascontiguousarray(cell_type, dtype=np.uint8)
+    H, W = t.shape
+    S = np.empty((H, W), np.float64)
+    a = np.empty((H, W), np.int32)
+    b = np.empty((H, W), np.int32)
+    src = None
+    if static_field is not None:
+        src = np.ascontiguousarray(static_field, dtype=np.float64)
+        if src.shape != t.shape:
+            raise ValueError("static_field must have the shape of cell_type")
+    bad = C.c_int64(-1)
+    rc = load().fast_floor_field(W, H, _ptr(t), _ptr(src), _ptr(S), _ptr(a), _ptr(b),
+                                          C.byref(bad))
+    if rc:
+        raise FastError(rc, f"fast_floor_field: cell {bad.value}")
+    return S, a, b
 
 
 # -- self tests of the device arithmetic ------------------------------------------

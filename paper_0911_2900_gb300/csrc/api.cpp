@@ -22,6 +22,8 @@
 
 namespace fastgb {
 int64_t exact_floor_field(int32_t W, int32_t H, const uint8_t* type, int32_t* a, int32_t* b);
+int64_t decompose_field(int32_t W, int32_t H, const uint8_t* type, const double* S, int32_t max_ab,
+                        int32_t* a, int32_t* b);
 }
 
 using namespace fastgb;
@@ -79,6 +81,10 @@ struct fast_ctx {
   MoveEntry* d_act[3] = {nullptr, nullptr, nullptr};
   uint32_t* d_mv_prio = nullptr;
   uint32_t* d_mv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  unsigned long long* d_flow_node = nullptr;  // dataflow schedule, per mover slot
+  uint32_t* d_flow_succ = nullptr;
+  int32_t* d_flow_cnt = nullptr;
+  uint32_t* d_flow_ovf = nullptr;
 
   uint32_t list_cap = 0;
   uint32_t* d_bucket = nullptr;
@@ -131,6 +137,7 @@ struct fast_ctx {
   int move_blocks = 0;
   int tile_shift = 4;
   int graph_steps = 512;  // longest step loop captured as one graph
+  int move_schedule = MOVE_FLOW;
   bool resort_pending = false;  // agents placed since the last spatial sort
 
   int64_t t_host = 0;
@@ -364,6 +371,10 @@ int rebuild_layout(fast_ctx* c) {
     dfree(c, c->d_act[0]);
     dfree(c, c->d_mv_prio);
     for (auto& p : c->d_mv) dfree(c, p);
+    dfree(c, c->d_flow_node);
+    dfree(c, c->d_flow_succ);
+    dfree(c, c->d_flow_cnt);
+    dfree(c, c->d_flow_ovf);
     const size_t n = (size_t)total_cap;
     if (int e = alloc_into(c, &c->d_queue, n)) return e;
     if (int e = alloc_into(c, &c->d_act[2], n)) return e;
@@ -371,6 +382,10 @@ int rebuild_layout(fast_ctx* c) {
     if (int e = alloc_into(c, &c->d_mv_prio, n)) return e;
     for (auto& p : c->d_mv)
       if (int e = alloc_into(c, &p, n)) return e;
+    if (int e = alloc_into(c, &c->d_flow_node, 6 * n)) return e;
+    if (int e = alloc_into(c, &c->d_flow_succ, 8 * n)) return e;
+    if (int e = alloc_into(c, &c->d_flow_cnt, n)) return e;
+    if (int e = alloc_into(c, &c->d_flow_ovf, n)) return e;
     c->list_cap = (uint32_t)total_cap;
   }
   // bucket offsets, 2 words per replicate, the scan's block sums (<= 1024)
@@ -405,6 +420,10 @@ StepArgs args_of(fast_ctx* c) {
   a.mv_ref = c->d_mv[1];
   a.mv_info = c->d_mv[2];
   a.act_cap = c->list_cap;
+  a.flow_node = c->d_flow_node;
+  a.flow_succ = c->d_flow_succ;
+  a.flow_cnt = c->d_flow_cnt;
+  a.flow_ovf = c->d_flow_ovf;
   a.dig_cell = c->d_dig_cell;
   a.dig_des = c->d_dig_des;
   a.dig_cap = c->dig_cap;
@@ -421,7 +440,9 @@ int plan_grid(fast_ctx* c, int n_chunks) { return std::max(1, std::min(n_chunks,
 // (the rounds are latency-bound), capped by the work and by the option.
 int move_grid(fast_ctx* c) {
   int g = 0;
-  if (move_rounds_max_grid(kMoveThreads, &g) != 0 || g <= 0) g = c->sms;
+  const int rc = c->move_schedule == MOVE_FLOW ? move_flow_max_grid(kMoveThreads, &g)
+                                               : move_rounds_max_grid(kMoveThreads, &g);
+  if (rc != 0 || g <= 0) g = c->sms;
   if (c->move_blocks > 0) g = std::min(g, c->move_blocks);
   return std::max(g, 1);
 }
@@ -460,7 +481,12 @@ int enqueue_step(fast_ctx* c, bool resort) {
   if (c->digests) LAUNCH_TRY(c, digest_des_launch(a, all, plan_grid(c, all.n), c->cur));
   LAUNCH_TRY(c, move_prep_launch(a, all, plan_grid(c, all.n), c->cur));
   CUDA_TRY(c, record_event(c, 3));
-  LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), kMoveThreads, c->cur));
+  if (c->move_schedule == MOVE_FLOW) {
+    LAUNCH_TRY(c, move_flow_launch(a, move_grid(c), kMoveThreads, c->cur));
+    c->launches += 1;  // move_flow_launch queues two kernels
+  } else {
+    LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), kMoveThreads, c->cur));
+  }
   CUDA_TRY(c, record_event(c, 4));
   if (c->digests) {
     LAUNCH_TRY(c, digest_cell_launch(a, all, plan_grid(c, all.n), c->cur));
@@ -667,7 +693,18 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   if (exits == 0) return fail(c, FAST_EINVAL, "grid has no exit cell");
 
   std::vector<int32_t> a(C), b(C);
-  exact_floor_field(g->width, g->height, g->cell_type, a.data(), b.data());
+  if (g->static_field) {
+    const int64_t bad = decompose_field(g->width, g->height, g->cell_type, g->static_field, 0x7FFE,
+                                        a.data(), b.data());
+    if (bad >= 0)
+      return fail(c, FAST_EINVAL,
+                  "static_field at cell %lld (%.17g): an exit needs 0, a free cell +inf "
+                  "(no exit reachable) or a + b*sqrt(2) rounded as fl(a + fl(b*sqrt2)), "
+                  "integers 0 <= a, b <= 32766, not both 0",
+                  (long long)bad, g->static_field[bad]);
+  } else {
+    exact_floor_field(g->width, g->height, g->cell_type, a.data(), b.data());
+  }
   std::vector<uint32_t> rec(C);
   RepHost& R = c->reps[r];
   for (int64_t i = 0; i < C; ++i) {
@@ -692,7 +729,9 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   R.speed_set = 0;
   for (auto& p : R.d.claim) dfree(c, p);
   dfree(c, R.d.cmark);
+  dfree(c, R.d.head);
   R.d.cmark = nullptr;
+  R.d.head = nullptr;
   R.d.rec = nullptr;
   R.d.mask = nullptr;
   R.d.claim[0] = R.d.claim[1] = nullptr;
@@ -709,6 +748,7 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   for (auto& p : R.d.claim)
     if (int e = alloc_into(c, &p, claim_cells)) return e;
   if (int e = alloc_into(c, &R.d.cmark, claim_cells)) return e;
+  if (int e = alloc_into(c, &R.d.head, claim_cells)) return e;
   RepDev& d = R.d;
   d.W = R.W;
   d.H = R.H;
@@ -727,6 +767,7 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   d.claim_tx = (R.W + 15) / 16;
   for (auto p : d.claim) CUDA_TRY(c, cudaMemsetAsync(p, 0xFF, claim_cells * 4, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(d.cmark, 0, claim_cells, c->stream));
+  CUDA_TRY(c, cudaMemsetAsync(d.head, 0, claim_cells * 8, c->stream));
   R.grid_set = true;
   R.placed = false;
   R.n = 0;
@@ -1461,7 +1502,11 @@ int fast_plan_noalloc(fast_ctx* c, int32_t r, int32_t step, int32_t id_bound,
   const int rc = noalloc_plan_launch(R.d, R.cap, step, desired_by_id_dev, id_bound, c->sms,
                                      c->stream);
   if (rc == -1) return fail(c, FAST_ECUDA, "address of the fixed re-check queue unavailable");
-  if (rc != 0) return fail(c, FAST_ECUDA, "launch of the allocation-free planning pass failed");
+  if (rc == -2) return fail(c, FAST_EINVAL, "replicate %d has too many agent slots", r);
+  if (rc != 0)
+    return fail(c, FAST_ECUDA,
+                "allocation-free planning pass not queued: a CUDA error was pending, a launch "
+                "failed, or the replicate's speed or reach set is unknown");
   return FAST_OK;
 }
 
@@ -1512,6 +1557,20 @@ int fast_set_option(fast_ctx* c, int32_t option, int64_t value) {
       }
       if (int e = write_ctl_int(c, offsetof(Ctl, claim_tag), (int32_t)value)) return e;
       break;
+    case FAST_OPT_MOVE_SCHEDULE:
+      if (value != MOVE_ROUNDS && value != MOVE_FLOW)
+        return fail(c, FAST_EINVAL, "move schedule must be 0 (rounds) or 1 (dataflow)");
+      c->move_schedule = (int)value;
+      break;
+    case FAST_OPT_FLOW_LIST_CAP:
+      if (value < 0 || value > kFlowQ) return fail(c, FAST_EINVAL, "list capacity not in 0..%d", kFlowQ);
+      if (int e = write_ctl_int(c, offsetof(Ctl, flow_qcap), (int32_t)value)) return e;
+      break;
+    case FAST_OPT_FLOW_TAG:
+      if (value < 0 || value > (int64_t)kFlowEpochWrap)
+        return fail(c, FAST_EINVAL, "list tag not in 0..%u", kFlowEpochWrap);
+      if (int e = write_ctl_int(c, offsetof(Ctl, move_epoch), (int32_t)(uint32_t)value)) return e;
+      break;
     case FAST_OPT_GRAPH_STEPS:
       if (value < 0 || value > 4096) return fail(c, FAST_EINVAL, "graph steps not in 0..4096");
       c->graph_steps = (int)value;
@@ -1544,6 +1603,39 @@ void fast_destroy(fast_ctx* c) {
   for (auto& kv : c->live) ptrs.push_back(kv.first);
   for (void* p : ptrs) dfree(c, p);
   delete c;
+}
+
+int fast_floor_field(int32_t width, int32_t height, const uint8_t* cell_type,
+                     const double* static_field, double* S_out, int32_t* a_out, int32_t* b_out,
+                     int64_t* bad_cell) {
+  if (bad_cell) *bad_cell = -1;
+  if (width < 1 || height < 1 || width > 65535 || height > 65535 ||
+      (int64_t)width * height >= ((int64_t)1 << 31) || !cell_type)
+    return FAST_EINVAL;
+  const int64_t C = (int64_t)width * height;
+  for (int64_t i = 0; i < C; ++i)
+    if (cell_type[i] > 2) {
+      if (bad_cell) *bad_cell = i;
+      return FAST_EINVAL;
+    }
+  std::vector<int32_t> a(C), b(C);
+  if (static_field) {
+    const int64_t bad = decompose_field(width, height, cell_type, static_field, 0x7FFE, a.data(),
+                                        b.data());
+    if (bad >= 0) {
+      if (bad_cell) *bad_cell = bad;
+      return FAST_EINVAL;
+    }
+  } else {
+    exact_floor_field(width, height, cell_type, a.data(), b.data());
+  }
+  for (int64_t i = 0; i < C; ++i) {
+    if (S_out)
+      S_out[i] = a[i] < 0 ? HUGE_VAL : (double)a[i] + (double)b[i] * kSqrt2;
+    if (a_out) a_out[i] = a[i];
+    if (b_out) b_out[i] = b[i];
+  }
+  return FAST_OK;
 }
 
 // ---- self tests ------------------------------------------------------------

@@ -11,8 +11,10 @@
 // is reached all its cells are final, and each relaxation lands in bucket
 // k+1 or k+2 (edge costs < 2), so three buckets in a ring suffice.  Inside a
 // bucket the exact (a, b) minimum of every cell is kept by exact comparison.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <utility>
 #include <vector>
 
 namespace fastgb {
@@ -87,6 +89,70 @@ int64_t exact_floor_field(int32_t W, int32_t H, const uint8_t* type, int32_t* a,
     ++k;
   }
   return reached;
+}
+
+// A caller's floor field S (doubles, row-major) as exact step counts: for
+// every reachable cell the integers 0 <= a, b <= max_ab with
+// S == fl(a + fl(b * sqrt2)), the rounding the FP64 rule applies to (a, b).
+// sqrt2 being irrational, two pairs with b <= 2^15 differ by more than about
+// 1e-5, far above the rounding of S, so the pair is unique when it exists.
+// Walls: a = b = -1 whatever S says.  Exit cells must have S == 0 (a = b = 0);
+// a free cell with S == +inf is one no exit can be reached from (a = b = -1);
+// any other free cell must have a positive S of that form.  Returns the index
+// of the first cell that breaks these rules, or -1.
+int64_t decompose_field(int32_t W, int32_t H, const uint8_t* type, const double* S, int32_t max_ab,
+                        int32_t* a, int32_t* b) {
+  const double kR2 = 1.4142135623730951;  // the double nearest sqrt2
+  std::vector<double> tb((size_t)max_ab + 1);
+  std::vector<std::pair<double, int32_t>> fr((size_t)max_ab + 1);
+  for (int32_t j = 0; j <= max_ab; ++j) {
+    tb[j] = (double)j * kR2;
+    fr[j] = {tb[j] - std::floor(tb[j]), j};
+  }
+  std::sort(fr.begin(), fr.end());
+  // does b = j give an integer a in range with fl(a + tb[j]) == s?
+  auto fits = [&](double s, int32_t j, int32_t* ao) {
+    if (j < 0 || j > max_ab || tb[j] > s + 0.5) return false;
+    const double af = std::nearbyint(s - tb[j]);
+    if (af < 0.0 || af > (double)max_ab) return false;
+    if ((double)(int32_t)af + tb[j] != s) return false;
+    *ao = (int32_t)af;
+    return true;
+  };
+  const int64_t C = (int64_t)W * H;
+  int32_t hint = 0;
+  for (int64_t c = 0; c < C; ++c) {
+    a[c] = b[c] = -1;
+    const double s = S[c];
+    if (type[c] == 1) continue;
+    if (type[c] == 2) {
+      if (s != 0.0) return c;
+      a[c] = b[c] = 0;
+      continue;
+    }
+    if (std::isinf(s) && s > 0.0) continue;  // no exit reachable: a wall
+    if (!(s > 0.0) || !std::isfinite(s)) return c;
+    int32_t ao = -1, bo = -1;
+    // neighbouring cells mostly differ by a step or two in b
+    for (int32_t d = 0; d <= 4 && bo < 0; ++d) {
+      if (fits(s, hint + d, &ao)) bo = hint + d;
+      else if (d > 0 && fits(s, hint - d, &ao)) bo = hint - d;
+    }
+    if (bo < 0) {
+      // every b whose fractional part of fl(b sqrt2) is within 1e-6 of S's
+      const double f = s - std::floor(s);
+      for (double g : {f, f - 1.0, f + 1.0}) {
+        auto it = std::lower_bound(fr.begin(), fr.end(), std::make_pair(g - 1e-6, (int32_t)-1));
+        for (; it != fr.end() && it->first <= g + 1e-6 && bo < 0; ++it)
+          if (fits(s, it->second, &ao)) bo = it->second;
+      }
+    }
+    if (bo < 0) return c;
+    a[c] = ao;
+    b[c] = bo;
+    hint = bo;
+  }
+  return -1;
 }
 
 }  // namespace fastgb

@@ -11,9 +11,14 @@
 // carries in the device's global memory for as long as it is loaded.
 //
 // What it computes: the desired cell of every agent of one replicate for a
-// given step -- FP32 weights, margin test, FP64 re-check of the draws inside
-// the margin -- the same values as a planning pass of the context, written by
-// agent id into the caller's buffer.  The context's own state is not touched.
+// given step -- FP32 weights, margin test (the same draw and margin code as
+// the context's planning kernels), FP64 re-check of the draws inside the
+// margin -- written by agent id into the caller's buffer.  It always plans
+// this way, whatever precision the context was created with, so its output
+// is the FP64 rule's choice: equal to a planning pass of an FP64 or an
+// FP32-with-re-check context (an FP32-without-re-check context, a
+// diagnostic mode, may choose differently near a boundary).  The context's
+// own state is not touched.
 //
 // Limits: at most kNoAllocMaxAgents agent slots per replicate (the queue must
 // hold every agent in the worst case).  Every call on a device shares the one
@@ -65,24 +70,10 @@ __global__ void __launch_bounds__(128) k_noalloc_plan(RepDev R, int32_t cap, int
       w[k] = wk;
       Wt += wk;
     }
-    const float r = __fmul_rn(plan_uniform24((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi),
-                              Wt);
-    float c = 0.f, cprev = 0.f, ck = 0.f;
-    int found = -1;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      if (w[k] > 0.f) {
-        const float cn = c + w[k];
-        if (found < 0 && r < cn) {
-          found = k;
-          cprev = c;
-          ck = cn;
-        }
-        c = cn;
-      }
-    }
-    const float mw = R.margin * Wt;
-    if (found >= 0 && r > cprev + mw && r < ck - mw) {
+    const float u = plan_uniform24((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
+    bool certain = false;
+    const int found = fp32_pick<K>(Wt, u, R.margin, [&](int k) { return w[k]; }, certain);
+    if (certain) {
       if (id < bound) out[id] = cell + s_off[found];
     } else {
       const uint32_t q = atomicAdd(&scratch[0], 1u);
@@ -162,32 +153,50 @@ static int noalloc_scratch(uint32_t** out) {
   return 0;
 }
 
+// Launches the FP32 pass for the replicate's speed; false for a speed
+// outside 1..5 (nothing launched).
 template <int REACH>
-static void launch_noalloc_v(const RepDev& R, int32_t cap, int32_t t, int32_t* out, int32_t bound,
+static bool launch_noalloc_v(const RepDev& R, int32_t cap, int32_t t, int32_t* out, int32_t bound,
                              uint32_t* sc, int grid, cudaStream_t s) {
   switch (R.v) {
-    case 1: k_noalloc_plan<1, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); break;
-    case 2: k_noalloc_plan<2, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); break;
-    case 3: k_noalloc_plan<3, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); break;
-    case 4: k_noalloc_plan<4, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); break;
-    case 5: k_noalloc_plan<5, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); break;
+    case 1: k_noalloc_plan<1, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); return true;
+    case 2: k_noalloc_plan<2, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); return true;
+    case 3: k_noalloc_plan<3, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); return true;
+    case 4: k_noalloc_plan<4, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); return true;
+    case 5: k_noalloc_plan<5, REACH><<<grid, 128, 0, s>>>(R, cap, t, out, bound, sc); return true;
   }
+  return false;
 }
 
 // Returns 0, -1 (scratch address unavailable), -2 (too many agent slots) or
-// -3 (launch error).
+// -3 (an error was already pending on this thread, a launch failed, or the
+// replicate's speed or reach set is unknown, so that nothing was launched).
+// Launch errors are read with cudaPeekAtLastError, so that an error another
+// caller left pending is not taken (and cleared) as this pass's own; an
+// error of this pass's own launches is cleared after it is reported.
 int noalloc_plan_launch(const RepDev& R, int32_t cap, int32_t t, int32_t* out, int32_t bound,
                         int sms, cudaStream_t s) {
   if (cap > kNoAllocMaxAgents) return -2;
+  if (cudaPeekAtLastError() != cudaSuccess) return -3;
   uint32_t* sc = nullptr;
   if (noalloc_scratch(&sc) != 0) return -1;
   if (cudaMemsetAsync(sc, 0, sizeof(uint32_t), s) != cudaSuccess) return -3;
   const int grid = std::max(1, std::min((cap + 127) / 128, sms * 8));
-  if (R.reach == REACH_L2) launch_noalloc_v<REACH_L2>(R, cap, t, out, bound, sc, grid, s);
-  if (R.reach == REACH_L2P) launch_noalloc_v<REACH_L2P>(R, cap, t, out, bound, sc, grid, s);
-  if (R.reach == REACH_LINF) launch_noalloc_v<REACH_LINF>(R, cap, t, out, bound, sc, grid, s);
+  bool launched = false;
+  if (R.reach == REACH_L2) launched = launch_noalloc_v<REACH_L2>(R, cap, t, out, bound, sc, grid, s);
+  if (R.reach == REACH_L2P) launched = launch_noalloc_v<REACH_L2P>(R, cap, t, out, bound, sc, grid, s);
+  if (R.reach == REACH_LINF) launched = launch_noalloc_v<REACH_LINF>(R, cap, t, out, bound, sc, grid, s);
+  if (!launched) return -3;
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return -3;
+  }
   k_noalloc_recheck<<<std::max(1, sms * 4), 64, 0, s>>>(R, t, out, bound, sc);
-  return cudaGetLastError() == cudaSuccess ? 0 : -3;
+  if (cudaPeekAtLastError() != cudaSuccess) {
+    cudaGetLastError();
+    return -3;
+  }
+  return 0;
 }
 
 int noalloc_max_agents() { return kNoAllocMaxAgents; }

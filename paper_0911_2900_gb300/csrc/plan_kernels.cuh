@@ -108,14 +108,15 @@ __device__ __forceinline__ float rec_weight(uint32_t r, float a0m, float b0m, fl
   return (r & REC_OCC) ? 0.f : ex2_approx(ds32_rec(r, a0m, b0m) * c32);
 }
 
-// Shared end of the one-thread kernels: the draw against the cumulative
-// weights w(k) (first k with r < C_k; zero weights leave C unchanged and so
-// are never first; no such k only through rounding, which the FP64 rule then
-// settles), the margin test, and the outputs.
-template <int K, int CENTER, bool DIAG, typename WF>
-__device__ __forceinline__ void finish_g1(const StepArgs& a, const RepDev& R, int rep, int slot,
-                                          int cell, float Wt, float u, float margin,
-                                          int norecheck, const int* s_dxdy, WF w) {
+// The FP32 draw of one agent: r = u*W against the cumulative weights
+// C_k = w(0) + ... + w(k) in canonical order; the choice is the first k with
+// r < C_k (a zero weight leaves C unchanged and so is never first; no such k
+// only through rounding, which the FP64 rule then settles).  Returns k (-1:
+// none) and sets `certain` when r lies farther than margin*W from both
+// boundaries C_{k-1} and C_k of that k: only then is the FP32 choice sure to
+// be the FP64 rule's (the margin bounds the FP32 weights' and sums' error).
+template <int K, typename WF>
+__device__ __forceinline__ int fp32_pick(float Wt, float u, float margin, WF w, bool& certain) {
   const float r = __fmul_rn(u, Wt);
   float cacc = 0.f, cprev = 0.f, ck = 0.f;
   int found = -1;
@@ -128,6 +129,19 @@ __device__ __forceinline__ void finish_g1(const StepArgs& a, const RepDev& R, in
     ck = hit ? cn : ck;
     cacc = cn;
   }
+  const float mw = margin * Wt;
+  certain = (found >= 0) && (r > cprev + mw) && (r < ck - mw);
+  return found;
+}
+
+// Shared end of the one-thread kernels: the draw and margin test
+// (fp32_pick), and the outputs.
+template <int K, int CENTER, bool DIAG, typename WF>
+__device__ __forceinline__ void finish_g1(const StepArgs& a, const RepDev& R, int rep, int slot,
+                                          int cell, float Wt, float u, float margin,
+                                          int norecheck, const int* s_dxdy, WF w) {
+  bool ok = false;
+  const int found = fp32_pick<K>(Wt, u, margin, w, ok);
   if (DIAG) {
     float* dp = a.diag_p32 + (a.diag_base[rep] + slot) * (int64_t)kMaxK;
     float cc = 0.f;
@@ -137,8 +151,6 @@ __device__ __forceinline__ void finish_g1(const StepArgs& a, const RepDev& R, in
       dp[k] = cc / Wt;
     }
   }
-  const float mw = margin * Wt;
-  const bool ok = (found >= 0) && (r > cprev + mw) && (r < ck - mw);
   const int dd = s_dxdy[found >= 0 ? found : CENTER];
   const int target = cell + ((dd >> 8) - 16) * R.W + ((dd & 0xFF) - 16);
   if (DIAG) {

@@ -75,3 +75,33 @@ def test_create_rejects_bad_arguments(lib):
     assert lib.fast_create(C.byref(h), 1, 7, 0, None, None, None, None) == -1
     assert lib.fast_create(C.byref(h), 1, 1, 9, None, None, None, None) == -1
     assert lib.fast_create(C.byref(h), 300, 1, 0, None, None, None, None) == -1
+
+
+def test_plan_noalloc_checks_the_output_tensor():
+    """The allocation-free pass writes by agent id through a raw device
+    pointer, which the C side cannot check: the binding refuses a tensor of
+    another dtype, a non-contiguous view and one that is not on the
+    context's CUDA device, before any call into the library (no GPU needed:
+    the refusals come first)."""
+    import torch
+
+    import paper_0911_2900_gb300 as fg
+
+    class NoLib:
+        def __getattr__(self, name):
+            raise AssertionError(f"the library was called ({name})")
+
+    ctx = object.__new__(fg.Context)
+    ctx.lib, ctx.h, ctx.device = NoLib(), None, torch.device("cuda", 0)
+    with pytest.raises(ValueError, match="torch tensor"):
+        ctx.plan_noalloc(0, 0, [0, 1, 2])
+    with pytest.raises(ValueError, match="int32"):
+        ctx.plan_noalloc(0, 0, torch.zeros(8, dtype=torch.int64))
+    with pytest.raises(ValueError, match="int32"):
+        ctx.plan_noalloc(0, 0, torch.zeros(8, dtype=torch.float32))
+    with pytest.raises(ValueError, match="contiguous"):
+        ctx.plan_noalloc(0, 0, torch.zeros(16, dtype=torch.int32)[::2])
+    with pytest.raises(ValueError, match="must be on"):
+        ctx.plan_noalloc(0, 0, torch.zeros(8, dtype=torch.int32))
+    with pytest.raises(ValueError, match="must be on"):
+        ctx.plan_noalloc(0, 0, torch.zeros(8, dtype=torch.int32, device="meta"))

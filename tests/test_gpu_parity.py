@@ -33,8 +33,10 @@ def fg():
 
 def run_gpu(fg, works, steps, precision="fp32_recheck", reach="l2", digests=True, resort=8,
             graph=True, id_perm=None, start_step=0, lanes=None, tile_shift=None, chunks=None,
-            graph_steps=None, tune=None, speeds=None):
+            graph_steps=None, tune=None, speeds=None, options=None):
     ctx = fg.Context(len(works), precision, reach)
+    for name, value in (options or {}).items():
+        ctx.set_option(name, value)
     ctx.set_option("digests", 1 if digests else 0)
     ctx.set_option("resort_period", resort)
     ctx.set_option("use_graph", 1 if graph else 0)
@@ -136,28 +138,25 @@ def test_grid_barrier_sums_counts_exactly(fg, per_sm):
 # --------------------------------------------------------------------------- parity
 @pytest.mark.parametrize("precision", ["fp64", "fp32_recheck"])
 def test_room200_2k_v4(fg, orc, precision):
+    """The plain-method workload (200x200 room, one exit, 2,000 agents,
+    v_m=4) for the paper's whole run of 396 steps (Sec. 2), in both
+    precisions."""
     w = wl.config_small_room()
-    steps = 396 if precision == "fp64" else 120
+    steps = 396
     _, (g,) = run_gpu(fg, [w], steps, precision)
-    o = run_oracle(orc, w, steps)
+    o = run_oracle(orc, w, steps, threads=os.cpu_count() or 1)
     assert_same(g, o, steps)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32_recheck"])
 @pytest.mark.parametrize("v", [1, 2, 3, 4, 5])
-def test_corridors_40k_vsweep_fp64(fg, orc, v):
+def test_corridors_40k_vsweep(fg, orc, v, precision):
+    """The v_m sweep workload (1000x500 room and corridors, 40,000 agents)
+    at every v_m for all 396 steps, in both precisions."""
     w = wl.config_corridors(v_m=v)
-    steps = 12
-    _, (g,) = run_gpu(fg, [w], steps, "fp64")
-    o = run_oracle(orc, w, steps)
-    assert_same(g, o, steps)
-
-
-@pytest.mark.parametrize("v", [1, 3, 5])
-def test_corridors_40k_fp32_recheck(fg, orc, v):
-    w = wl.config_corridors(v_m=v)
-    steps = 12
-    _, (g,) = run_gpu(fg, [w], steps, "fp32_recheck")
-    o = run_oracle(orc, w, steps)
+    steps = 396
+    _, (g,) = run_gpu(fg, [w], steps, precision)
+    o = run_oracle(orc, w, steps, threads=os.cpu_count() or 1)
     assert_same(g, o, steps)
 
 
@@ -181,6 +180,43 @@ def test_lanes_per_agent_variants(fg, orc, lanes, v):
     _, (g,) = run_gpu(fg, [w], steps, "fp32_recheck", lanes={v: lanes})
     o = run_oracle(orc, w, steps)
     assert_same(g, o, steps)
+
+
+def test_caller_floor_field(fg, orc):
+    """A caller's static floor field (fast_grid_desc.static_field): the
+    library's own field passed back gives the same trajectories, and a field
+    computed around a wall that is not in the grid (agents are steered
+    around it but may cross it) gives the oracle's trajectories with the same
+    field."""
+    t = wl.room(90, 70)
+    wl.add_exit(t, "bottom", 40, 4)
+    wl.add_exit(t, "left", 20, 3)
+    cells = wl.place_uniform(t, 2500, 5)
+    tv = t.copy()
+    tv[35, 10:80] = wl.WALL
+    _, _, vS = orc.floor_field(tv)
+    vS[35, 10:80] = 500.0 + 3 * np.sqrt(2.0)
+    S0 = fg.floor_field(t)[0]
+    steps = 60
+    for field in (S0, vS):
+        w = wl.Workload("field", t, cells, 4, seed=77)
+        ctx = fg.Context(1, "fp32_recheck")
+        ctx.set_option("digests", 1)
+        ctx.init_grid(0, t, w.k_S, w.v_m, w.seed, static_field=field)
+        ctx.place(0, cells)
+        ctx.step(steps)
+        c, d, st = ctx.readback(0, len(cells))
+        dc, dd = ctx.digests(0, steps)
+        sim = orc.Sim(t, v=4, kS=w.k_S, seed=w.seed, S=field)
+        sim.place(cells)
+        r = sim.run(0, steps, threads=os.cpu_count() or 1)
+        o = dict(cells=sim.cells_by_id(), desired=r["desired"], dig_cell=r["dig_cell"],
+                 dig_des=r["dig_des"])
+        assert_same(dict(cells=c, desired=d, stats=st, dig_cell=dc, dig_des=dd), o, steps)
+    with pytest.raises(fg.FastError):
+        bad = S0.copy()
+        bad[10, 10] += 1e-9
+        fg.Context(1, "fp32_recheck").init_grid(0, t, 1.2, 4, 0, static_field=bad)
 
 
 @pytest.mark.parametrize("k_S", [0.0, 0.35, 5.0])
@@ -230,6 +266,7 @@ def test_claim_tag_cleanups(fg, orc, reserve, tag):
     steps = 20
     o = run_oracle(orc, w, steps)
     ctx = fg.Context(1, "fp32_recheck")
+    ctx.set_option("move_schedule", 0)
     ctx.set_option("digests", 1)
     ctx.set_option("claim_reserve", reserve)
     ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
@@ -241,6 +278,32 @@ def test_claim_tag_cleanups(fg, orc, reserve, tag):
     cells, des, st = ctx.readback(0, len(w.cells))
     dc, dd = ctx.digests(0, steps)
     assert_same(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd), o, steps)
+
+
+@pytest.mark.parametrize("options", [
+    dict(move_schedule=0),                      # rounds of claims, a grid barrier each
+    dict(move_schedule=1),                      # the dataflow schedule (default)
+    dict(flow_list_cap=1),                      # nearly every release spills: waves
+    dict(flow_list_cap=7),
+    dict(flow_tag=0xFFFFFF00 - 3),              # list-head tags restart within the run
+])
+def test_move_schedules(fg, orc, options):
+    """Both schedules of the sequential movement, the dataflow schedule with
+    shared-memory lists so small that released movers spill into the global
+    overflow list (and are moved in waves after grid barriers), and list-head
+    tags that run out and restart: the oracle's trajectories every time, on a
+    dense room (long priority chains) and a batch of replicates."""
+    t2 = wl.room(40, 32)
+    wl.add_exit(t2, "left", 12, 3)
+    wl.add_exit(t2, "top", 20, 2)
+    free = np.flatnonzero(t2.ravel() == wl.FREE)
+    cells = np.sort(np.random.default_rng(9).choice(free, int(0.8 * len(free)), replace=False))
+    dense = wl.Workload("dense", t2, cells.astype(np.int32), 5, seed=12)
+    works = [dense] + wl.config_batch(n_rep=3, seed=17, cells_hi=200 ** 2, agents_hi=4000)
+    steps = 40
+    _, gs = run_gpu(fg, works, steps, "fp32_recheck", options=options)
+    for w, g in zip(works, gs):
+        assert_same(g, run_oracle(orc, w, steps), steps)
 
 
 def test_autotune_changes_speed_not_results(fg, orc):
@@ -386,14 +449,23 @@ def test_invalid_inputs_are_rejected(fg):
 
 
 # --------------------------------------------------------------------------- full size
-def test_batched_form_full_size_sampled(fg, orc):
-    """256 replicates of the batched form (grids 100^2..2000^2 cells, 1e3..1e5
-    agents, v_m 1..5) in one context, autotuned, the step loop as one graph:
-    after 8 steps, replicates sampled across sizes and every v_m match the
-    oracle run from the same start for all 8 steps, and every replicate keeps
-    the conservation invariants."""
+def oracle_batch(orc, works, steps):
+    """The oracle on every replicate, several replicates at a time on host
+    threads (the C oracle releases the interpreter lock; no process fork)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 1) as ex:
+        return list(ex.map(lambda w: run_oracle(orc, w, steps, threads=1), works))
+
+
+def test_batched_form_full_size(fg, orc):
+    """All 256 replicates of the batched form (grids 100^2..2000^2 cells,
+    1e3..1e5 agents, v_m 1..5) in one context, autotuned, the step loop as
+    one graph launch as the benchmark runs it: every replicate's per-step
+    desired and cell digests and its final positions and desired cells equal
+    the oracle's, run from the same start, for 40 steps."""
     works = wl.config_batch()
-    steps = 8
+    steps = 40
     ctx = fg.Context(len(works), "fp32_recheck")
     ctx.set_option("digests", 1)
     for r, w in enumerate(works):
@@ -401,127 +473,56 @@ def test_batched_form_full_size_sampled(fg, orc):
         ctx.place(r, w.cells)
     ctx.autotune(trials=2)
     ctx.step(steps)
-    order = np.argsort([len(w.cells) for w in works])
-    sample = {int(order[0]), int(order[len(order) // 2]), int(order[-1])}
-    for v in range(1, 6):
-        sample.add(next(r for r, w in enumerate(works) if w.v_m == v))
-    for r, w in enumerate(works):
-        cells, _, st = ctx.readback(r, len(w.cells))
-        alive = cells >= 0
-        assert st["alive"] + st["exited"] == len(w.cells) and st["alive"] == int(alive.sum())
-        assert len(np.unique(cells[alive])) == int(alive.sum())
-        assert (w.cell_type.ravel()[cells[alive]] == wl.FREE).all()
-        if r in sample:
-            dc, dd = ctx.digests(r, steps)
-            o = run_oracle(orc, w, steps, threads=os.cpu_count() or 1)
-            assert np.array_equal(dd, o["dig_des"]) and np.array_equal(dc, o["dig_cell"]), r
-            assert np.array_equal(cells, o["cells"]), r
+    outs = oracle_batch(orc, works, steps)
+    for r, (w, o) in enumerate(zip(works, outs)):
+        cells, des, st = ctx.readback(r, len(w.cells))
+        dc, dd = ctx.digests(r, steps)
+        assert_same(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd), o, steps)
+        assert st["alive"] + st["exited"] == len(w.cells)
 
-def test_precision_form_full_size_one_step(fg, orc):
-    """4000x4000, 1M clustered agents, v_m=4, FP32 + FP64 re-check, in the
-    launch configuration the benchmark times: after 3 steps, the next step's
-    desired cells and positions equal the oracle's for every agent; the
-    FP32-only draw flips only inside the margin."""
+
+def test_precision_form_full_length(fg, orc):
+    """4000x4000, 1M clustered agents, v_m=4, FP32 + FP64 re-check, autotuned
+    as the benchmark runs it, for the paper's whole run of 396 steps from the
+    workload's own start: per-step digests of desired cells and positions,
+    and the final arrays, equal the oracle's for every agent and step.  The
+    FP32-only draws of the first step flip only inside the margin."""
     w = wl.config_precision()
-    ctx, (g3,) = run_gpu(fg, [w], 3, "fp32_recheck", digests=False)
+    steps = 396
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.set_option("digests", 1)
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx.place(0, w.cells)
+    ctx.autotune(trials=2)
     rep = ctx.precision_report()
     assert rep["flips_unflagged"] == 0
     assert rep["flagged"] < 0.01 * rep["agents"]
-    alive = np.flatnonzero(g3["cells"] >= 0).astype(np.int32)
-    sim = orc.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed)
-    sim.place(g3["cells"][alive], ids=alive)
-    ctx.step(1)
-    cells, des, _ = ctx.readback(0, len(w.cells))
-    r = sim.run(3, 1, threads=os.cpu_count() or 1, digests=False)
-    want_des = np.full(len(w.cells), -1, np.int32)
-    want_des[alive] = r["desired"]
-    assert np.array_equal(des[cells >= 0], want_des[cells >= 0])
-    assert np.array_equal(cells, sim.cells_by_id())
+    ctx.step(steps)
+    cells, des, st = ctx.readback(0, len(w.cells))
+    dc, dd = ctx.digests(0, steps)
+    o = run_oracle(orc, w, steps, threads=os.cpu_count() or 1)
+    assert_same(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd), o, steps)
 
 
-def test_stress_form_full_size_one_step(fg, orc):
-    """16384x16384, 10M uniform agents, v_m=5, FP32 + FP64 re-check with the
-    spatial re-sort every 8 steps: after 7 steps, step 7 (which re-sorts at
-    its end) gives the oracle's desired cells and positions for every agent
-    when the oracle starts from the GPU's state; the FP32-only draw flips
-    only inside the margin."""
+def test_stress_form_from_start(fg, orc):
+    """16384x16384, 10M uniform agents, v_m=5, FP32 + FP64 re-check, spatial
+    re-sort every 8 steps: 24 steps from the workload's own start (three
+    re-sorts) with per-step digests and the final arrays equal to the
+    oracle's; the FP32-only draws of the first step flip only inside the
+    margin."""
     w = wl.config_stress()
-    ctx, (g7,) = run_gpu(fg, [w], 7, "fp32_recheck", digests=False)
+    steps = 24
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.set_option("digests", 1)
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx.place(0, w.cells)
     rep = ctx.precision_report()
     assert rep["flips_unflagged"] == 0
     assert rep["flagged"] < 0.02 * rep["agents"]
-    alive = np.flatnonzero(g7["cells"] >= 0).astype(np.int32)
-    sim = orc.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed)
-    sim.place(g7["cells"][alive], ids=alive)
-    ctx.step(1)
+    ctx.step(steps)
     cells, des, st = ctx.readback(0, len(w.cells))
-    r = sim.run(7, 1, threads=os.cpu_count() or 1, digests=False)
-    want_des = np.full(len(w.cells), -1, np.int32)
-    want_des[alive] = r["desired"]
-    assert np.array_equal(des[cells >= 0], want_des[cells >= 0])
-    assert np.array_equal(cells, sim.cells_by_id())
-    assert st["alive"] + st["exited"] == len(w.cells)
-
-
-# --------------------------------------------------------------------------- speeds per agent
-def _speeds(n, seed, lo=1, hi=5):
-    return np.random.default_rng(seed).integers(lo, hi + 1, n).astype(np.uint8)
-
-
-@pytest.mark.parametrize("precision,lanes", [("fp64", None), ("fp32_recheck", 0),
-                                             ("fp32_recheck", 1), ("fp32_recheck", 2),
-                                             ("fp32_recheck", 8)])
-def test_per_agent_speeds(fg, orc, precision, lanes):
-    """Agents of one replicate with maximum speeds 1..5 of their own: each
-    speed's planning launch plans only its agents, over its reach set and
-    line-of-sight mask; the re-sort keeps the speed classes apart; the FP64
-    re-check uses each agent's speed.  Bit-equal to the oracle."""
-    w = wl.config_small_room(W=80, H=60, n=1500, seed=21, v_m=3)
-    sp = _speeds(len(w.cells), 5)
-    lanes_by_v = None if lanes is None else {v: lanes for v in range(1, 6)}
-    steps = 60
-    _, (g,) = run_gpu(fg, [w], steps, precision, speeds=[sp], lanes=lanes_by_v)
-    o = run_oracle(orc, w, steps, speeds=sp)
-    assert_same(g, o, steps)
-
-
-def test_per_agent_speeds_batched_with_uniform_replicates(fg, orc):
-    """A batch mixing replicates with speeds per agent and replicates with one
-    speed: every replicate joins the planning launch of each speed it has."""
-    ws = [wl.config_small_room(W=50 + 10 * i, H=40, n=500 + 100 * i, seed=30 + i, v_m=1 + i)
-          for i in range(4)]
-    sps = [_speeds(len(ws[0].cells), 7, 2, 4), None, _speeds(len(ws[2].cells), 8), None]
-    steps = 40
-    _, gs = run_gpu(fg, ws, steps, "fp32_recheck", speeds=sps)
-    for w, sp, g in zip(ws, sps, gs):
-        assert_same(g, run_oracle(orc, w, steps, speeds=sp), steps)
-
-
-def test_speeds_equal_to_v_m_change_nothing(fg, orc):
-    w = wl.config_small_room(W=60, H=50, n=800, seed=41, v_m=4)
-    steps = 30
-    _, (a,) = run_gpu(fg, [w], steps)
-    _, (b,) = run_gpu(fg, [w], steps, speeds=[np.full(len(w.cells), 4, np.uint8)])
-    assert np.array_equal(a["dig_cell"], b["dig_cell"])
-    assert np.array_equal(a["dig_des"], b["dig_des"])
-    assert np.array_equal(a["cells"], b["cells"])
-
-
-def test_speeds_are_checked_by_the_library(fg):
-    w = wl.config_small_room(W=30, H=30, n=50, seed=2, v_m=2)
-    ctx = fg.Context(1, "fp32_recheck")
-    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
-    with pytest.raises(fg.FastError):
-        ctx.set_speeds(0, np.array([1, 0, 3], np.uint8))  # speed 0
-    with pytest.raises(fg.FastError):
-        ctx.set_speeds(0, np.array([6], np.uint8))  # speed 6
-    ctx.set_speeds(0, np.full(10, 3, np.uint8))  # fewer ids than agents
-    with pytest.raises(fg.FastError):
-        ctx.place(0, w.cells)
-    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)  # drops the speeds
-    ctx.set_speeds(0, np.full(len(w.cells), 3, np.uint8))
-    ctx.place(0, w.cells)
-    with pytest.raises(fg.FastError):
-        ctx.set_speeds(0, np.full(len(w.cells), 2, np.uint8))  # agents already placed
-    ctx.step(3)
+    dc, dd = ctx.digests(0, steps)
     ctx.close()
+    o = run_oracle(orc, w, steps, threads=os.cpu_count() or 1)
+    assert_same(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd), o, steps)
+    assert st["alive"] + st["exited"] == len(w.cells)
