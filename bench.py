@@ -103,7 +103,7 @@ def parse():
                    help="v_m of the room and corridors workloads (default 4)")
     p.add_argument("--fp64-steps", type=int, default=None,
                    help="steps of the all-FP64 form timed (default: --steps)")
-    p.add_argument("--move-schedule", default="flow", choices=["flow", "rounds"],
+    p.add_argument("--move-schedule", default="rounds", choices=["flow", "rounds"],
                    help="GPU schedule of the sequential movement (same results)")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-steps", type=int, default=2)
@@ -432,6 +432,7 @@ def bench_ours(args):
     mv_wait, mv_us = ctx.move_profile()
     ctx_phases = list(ctx.last_move_phases)
     ctx_block_max = list(ctx.last_move_block_max)
+    ctx_flow_stats = list(ctx.last_flow_stats)
     al1 = alive_now(ctx)
     b1 = union_bytes(ctx, al1)
     u1 = union_cells(ctx)
@@ -545,11 +546,14 @@ def bench_ours(args):
 
     ph = ctx_phases
     if flow:
-        move_last = {"pass1_us": round(ph[0] / 1e3, 2), "barrier_done_us": round(ph[1] / 1e3, 2),
-                     "pass2_us": round(ph[2] / 1e3, 2), "first_rounds_us": round(ph[3] / 1e3, 2),
-                     "movers_per_block_max": int(ph[4]),
-                     "waiting_after_pass2_block_max": int(ph[5]), "overflow_waves": int(ph[6]),
-                     "block_rounds_max": int(ph[7]), "times": "max over blocks, from kernel start"}
+        fs = ctx_flow_stats
+        move_last = {"phase_end_us": {k: round(ph[i] / 1e3, 2) for i, k in enumerate(
+                         ("list_pushes", "barrier", "list_walks", "block_rounds"))},
+                     "overflow_waves": int(ph[6]), "block_rounds_max": int(ph[7]),
+                     "longest_list": int(fs[0]), "list_nodes_walked": int(fs[1]),
+                     "movers_without_predecessor": int(fs[2]), "movers_released": int(fs[3]),
+                     "movers_per_block_max": int(fs[4]), "released_per_block_max": int(fs[5]),
+                     "times": "max over blocks, from the kernel's start"}
     else:
         move_last = {"waiting_after_round": [int(x) for x in mv_wait[:12]],
                      "round_us": [round(float(x), 2) for x in mv_us[:12]],

@@ -93,10 +93,10 @@ extern "C" {
                                   /* first claim tag, 0..254: a test hook for the   */
                                   /* clean-ups; results do not depend on it         */
 #define FAST_OPT_MOVE_SCHEDULE 17 /* how the sequential movement runs on the GPU    */
-                                  /* (same result either way): 1 (default) a        */
+                                  /* (same result either way): 0 (default) rounds   */
+                                  /* of claims, one grid barrier per round; 1 a     */
                                   /* dataflow over the conflict graph, one grid     */
-                                  /* barrier per step; 0 rounds of claims, one grid */
-                                  /* barrier per round                              */
+                                  /* barrier per step                               */
 #define FAST_OPT_FLOW_LIST_CAP 18 /* dataflow schedule: released movers a block     */
                                   /* keeps in shared memory per round, 1..8192     */
                                   /* (0: 8192); more spill into a global list that  */
@@ -277,7 +277,15 @@ int fast_phase_times(fast_ctx* ctx, float* ms5);
  * per block still waiting after the first round, the round from which one
  * block finished alone (0: none), 0.  With max_rounds >= 137, t_ns[73 + r]
  * also receives the most movers still waiting in one block after round r,
- * for the rounds written. */
+ * for the rounds written.  With max_rounds >= 143, t_ns[137..142] receive
+ * the dataflow schedule's counts of the step: the longest list walked, the
+ * list nodes all walks visited, the movers without predecessors, the movers
+ * released by a predecessor, the most movers of one block, the most movers
+ * released to one block.  The dataflow schedule's phase times (t_ns[65..72],
+ * max over blocks, ns from the kernel's start) are: list pushes done, grid
+ * barrier passed, list walks done, the block's own rounds done (t_ns[69..70]
+ * unused); then the overflow waves and the most rounds of one block
+ * (counts). */
 int fast_move_profile(fast_ctx* ctx, int32_t max_rounds, uint32_t* n_wait, uint64_t* t_ns);
 
 /* Runs the FP32 planning of the current state without re-check next to the

@@ -303,12 +303,13 @@ class Context:
 
     def move_profile(self):
         """(waiting agents after each round's claims, round durations in us) of the last step."""
-        n_wait = np.zeros(140, np.uint32)
-        t_ns = np.zeros(140, np.uint64)
-        r = self._check(self.lib.fast_move_profile(self.h, 137, _ptr(n_wait), _ptr(t_ns)),
+        n_wait = np.zeros(150, np.uint32)
+        t_ns = np.zeros(150, np.uint64)
+        r = self._check(self.lib.fast_move_profile(self.h, 143, _ptr(n_wait), _ptr(t_ns)),
                         "fast_move_profile")
         m = min(r, 64)
         self.last_move_phases = t_ns[65:73].astype(np.float64).copy()
+        self.last_flow_stats = t_ns[137:143].astype(np.int64).copy()
         self.last_move_block_max = t_ns[73:73 + m].astype(np.int64).copy()
         return n_wait[:m].copy(), np.diff(t_ns[:m + 1].astype(np.float64)) / 1e3
 

@@ -137,7 +137,7 @@ struct fast_ctx {
   int move_blocks = 0;
   int tile_shift = 4;
   int graph_steps = 512;  // longest step loop captured as one graph
-  int move_schedule = MOVE_FLOW;
+  int move_schedule = MOVE_ROUNDS;
   bool resort_pending = false;  // agents placed since the last spatial sort
 
   int64_t t_host = 0;
@@ -1387,6 +1387,8 @@ int fast_move_profile(fast_ctx* c, int32_t max_rounds, uint32_t* n_wait, uint64_
     for (int i = 0; i < 8; ++i) t_ns[65 + i] = h.phase_ns[i];
   if (t_ns && max_rounds >= 64 + 1 + 8 + 64)
     for (int i = 0; i < n; ++i) t_ns[73 + i] = h.round_bmax[i];
+  if (t_ns && max_rounds >= 64 + 1 + 8 + 64 + 6)
+    for (int i = 0; i < 6; ++i) t_ns[137 + i] = h.flow_stat[i];
   return h.rounds_last;
 }
 

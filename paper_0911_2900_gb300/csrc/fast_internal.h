@@ -90,6 +90,11 @@ struct Ctl {
   uint32_t ovf_count;         // dataflow schedule: released movers in the overflow list
   uint32_t flow_waves;        // dataflow schedule: overflow waves of the last step
   uint32_t pad3;
+  // dataflow schedule, last step: [0] longest list walked, [1] list nodes
+  // visited by all walks, [2] movers without predecessors, [3] movers
+  // released by a predecessor, [4] most movers of one block, [5] most
+  // movers released to one block
+  unsigned long long flow_stat[6];
   unsigned long long rounds_total;
   unsigned long long rechecked_total;
   unsigned long long agent_steps;

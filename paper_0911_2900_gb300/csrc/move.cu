@@ -102,8 +102,13 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
   if (epoch_ends(a.ctl)) clear_all_claims(a, false, true);
   // the dataflow schedule's list-head tags restart from clean heads
   if (__ldcg(&a.ctl->move_epoch) >= kFlowEpochWrap) clear_all_heads(a);
-  // the movement kernel gathers the step's round count from zero
-  if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->rounds_last = 0;
+  // the movement kernels gather the step's round count, phase times and
+  // statistics from zero
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ctl->rounds_last = 0;
+    for (int i = 0; i < 8; ++i) a.ctl->phase_ns[i] = 0ull;
+    for (int i = 0; i < 6; ++i) a.ctl->flow_stat[i] = 0ull;
+  }
   __shared__ uint32_t s_warp[8];
   __shared__ uint32_t s_base;
   const int t = a.ctl->t;
@@ -317,10 +322,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
   gl.L1 = a.mv_list[1] + start;
   if (tid < 2) s_cnt[tid] = 0u;
   const unsigned long long t_start = global_ns();
-  if (b == 0 && tid == 0) {
-    ctl->round_ns[0] = t_start;
-    for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = 0ull;
-  }
+  if (b == 0 && tid == 0) ctl->round_ns[0] = t_start;  // phase_ns: zeroed by k_move_prep
   // the per-block maxima are first written after the first grid barrier
   if (b == 0)
     for (int i = tid; i < kRoundLog; i += blockDim.x) ctl->round_bmax[i] = 0u;

@@ -18,12 +18,12 @@
 //   pass 2   every mover walks the lists of its cells: on each cell, whether
 //            some mover there comes before it (d counts such cells) and which
 //            mover comes right after it (its successor there); it stores its
-//            successors and adds d to its counter;
+//            successors and adds d to its counter (zeroed in pass 1);
 //   release  a mover that has moved takes one off the counter of its
 //            successor on each cell; whoever's operation leaves a counter at
 //            zero (the mover's own addition of d, or a predecessor's
-//            subtraction) owns that mover: in pass 2 it moves at once, else
-//            it goes on the owner block's list;
+//            subtraction) owns that mover: the thread moves one such mover
+//            next itself and puts the others on its block's list;
 //   rounds   a block moves its list in rounds separated by block barriers,
 //            until the list stays empty -- no block waits for another;
 //   waves    a full list spills into a global overflow list; after a grid
@@ -32,10 +32,12 @@
 // A counter receives +d once and -1 once from each of its d cells'
 // predecessors, in any order, so exactly one of those operations leaves it
 // at zero: each mover moves exactly once, after all its predecessors.
-// Counter updates are acquire-release atomics, so a mover's records are
-// read after every write of its predecessors.  A mover with d = 0 finds its
-// footprint as the movement-order pass read it and applies the outcome that
-// pass recorded (occupancy bits only).  Every wait is bounded: the grid
+// All counter updates are relaxed atomics: a fence before a mover's addition
+// publishes its successor list, a fence before a moved mover's subtractions
+// releases its writes, and the thread that moves a mover first reads its
+// counter with an acquire load.  A mover with d = 0 finds its footprint as
+// the movement-order pass read it and applies the outcome that pass
+// recorded (occupancy bits only).  Every wait is bounded: the grid
 // barrier has a time limit, list walks and rounds have length limits.
 #include "move_common.cuh"
 
@@ -45,15 +47,6 @@ constexpr uint32_t kEnd = 0xFFFFFFFFu;  // end of a list / no successor
 constexpr int kMaxWalk = 1024;          // nodes of one list (at most (2*5+1)^2 movers reach a cell)
 constexpr uint32_t kDeal = 32;          // movers dealt to the blocks at a time
 constexpr int kDevErrFlow = 7;          // device error: a list or the overflow list is corrupt
-
-__device__ __forceinline__ int atom_add_acqrel(int32_t* p, int32_t v) {
-  int32_t old;
-  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;"
-               : "=r"(old)
-               : "l"(__cvta_generic_to_global(p)), "r"(v)
-               : "memory");
-  return old;
-}
 
 // Tag of this pass's list heads: one more than the last pass's, restarting
 // at 1 once the movement-order pass has cleared the heads (it does so when
@@ -67,12 +60,13 @@ struct FlowBlock {
   uint32_t* list[2];  // shared memory, kFlowQ entries each
   uint32_t* cnt;      // shared: entries pushed onto each list (may exceed the capacity)
   uint32_t* ovf;      // shared: entries this block spilled since the last grid barrier
+  uint32_t* rel;      // shared: movers released to this block in the step
   uint32_t qcap;      // list capacity in use
 };
 
 // Hands mover j to this block: onto list `out`, or the overflow list.
-__device__ __forceinline__ void flow_push(const StepArgs& a, const FlowBlock& fb, int out,
-                                          uint32_t j) {
+__device__ __forceinline__ void flow_enqueue(const StepArgs& a, const FlowBlock& fb, int out,
+                                             uint32_t j) {
   const uint32_t pos = atomicAdd(&fb.cnt[out], 1u);
   if (pos < fb.qcap) {
     fb.list[out][pos] = j;
@@ -83,44 +77,83 @@ __device__ __forceinline__ void flow_push(const StepArgs& a, const FlowBlock& fb
   if (o < a.act_cap)
     a.flow_ovf[o] = j;
   else
-    atomicCAS(&a.ctl->err, 0, kDevErrFlow);  // cannot happen: each mover is released once
+    atomicCAS(&a.ctl->err, 0, kDevErrFlow);  // cannot happen: each mover is enqueued once
 }
 
-// After a mover has moved: one off the counter of its successor on each of
-// its cells; the successors whose counter this leaves at zero go to the block.
-__device__ __forceinline__ void flow_release(const StepArgs& a, const FlowBlock& fb, int out,
-                                             const uint32_t* sc) {
+// After a mover has moved and a fence has made its writes visible: one off
+// the counter of its successor on each of its cells (relaxed atomics; the
+// fence before them releases the mover's writes).  Returns one successor
+// this leaves at zero (kEnd: none), for the calling thread to move next; the
+// others go to the block.
+__device__ __forceinline__ uint32_t flow_release(const StepArgs& a, const FlowBlock& fb, int out,
+                                                 const uint32_t* sc) {
   int old[6];
 #pragma unroll
-  for (int s = 0; s < 6; ++s) old[s] = sc[s] != kEnd ? atom_add_acqrel(&a.flow_cnt[sc[s]], -1) : 0;
+  for (int s = 0; s < 6; ++s) old[s] = sc[s] != kEnd ? atomicSub(&a.flow_cnt[sc[s]], 1) : 0;
+  uint32_t next = kEnd;
 #pragma unroll
   for (int s = 0; s < 6; ++s)
-    if (sc[s] != kEnd && old[s] == 1) flow_push(a, fb, out, sc[s]);
+    if (sc[s] != kEnd && old[s] == 1) {
+      atomicAdd(fb.rel, 1u);
+      if (next == kEnd)
+        next = sc[s];
+      else
+        flow_enqueue(a, fb, out, sc[s]);
+    }
+  return next;
 }
 
-// Moves mover m, owned by this thread, whose predecessors have all moved:
-// reads the records of its walk afresh, commits, releases its successors.
-__device__ __forceinline__ void flow_move_released(const StepArgs& a, const PathTab* tab,
-                                                   const FlowBlock& fb, int out, uint32_t m) {
-  const MoveEntry e = a.act[2][m];
-  const int rep = (int)(e.ref >> 24), slot = (int)(e.ref & 0xFFFFFFu);
-  const RepDev& R = a.reps[rep];
-  int c[6], q[6];
-  foot_cells(tab, e.c0, R, e.info, c, q);
-  const int wl = walk_len(e.info);
-  uint32_t pr[6], sc[6];
+// A release-acquire fence at GPU scope: orders this thread's earlier memory
+// operations before its later ones as the release and acquire patterns of
+// the counters need (lighter than __threadfence, a sequentially consistent
+// fence).
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ int ld_acquire_s32(const int32_t* p) {
+  int32_t v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];"
+               : "=r"(v)
+               : "l"(__cvta_generic_to_global(p))
+               : "memory");
+  return v;
+}
+
+// Moves mover m, whose counter is at zero and which this thread owns, then
+// one after the other the successors each move leaves at zero (one per move;
+// the others go to the block).  Per move: an acquire load of the counter
+// orders the reads of the walk's records after every predecessor's writes
+// (a mover without predecessors applies the outcome the movement-order pass
+// recorded, reading nothing); a fence after the commit releases its writes
+// to the successors.
+__device__ __forceinline__ void flow_move_chain(const StepArgs& a, const PathTab* tab,
+                                                const FlowBlock& fb, int out, uint32_t m,
+                                                uint32_t limit) {
+  for (uint32_t hop = 0; m != kEnd; ++hop) {
+    if (hop > limit) {  // cannot happen: each mover moves once
+      atomicCAS(&a.ctl->err, 0, kDevErrRounds);
+      return;
+    }
+    const MoveEntry e = a.act[2][m];
+    const uint4 s03 = __ldcg(reinterpret_cast<const uint4*>(a.flow_succ) + 2 * (size_t)m);
+    const uint4 s47 = __ldcg(reinterpret_cast<const uint4*>(a.flow_succ) + 2 * (size_t)m + 1);
+    if (ld_acquire_s32(&a.flow_cnt[m]) != 0) atomicCAS(&a.ctl->err, 0, kDevErrFlow);
+    const int rep = (int)(e.ref >> 24), slot = (int)(e.ref & 0xFFFFFFu);
+    const RepDev& R = a.reps[rep];
+    int c[6], q[6];
+    foot_cells(tab, e.c0, R, e.info, c, q);
+    if (s47.z == 0u) {
+      commit_first(a, R, rep, slot, c, e.info);
+    } else {
+      const int wl = walk_len(e.info);
+      uint32_t pr[6];
 #pragma unroll
-  for (int s = 0; s < 6; ++s) pr[s] = (s <= wl) ? __ldcg(&R.rec[c[s]]) : REC_OCC;
-  const uint4 s03 = __ldcg(reinterpret_cast<const uint4*>(a.flow_succ) + 2 * (size_t)m);
-  const uint4 s47 = __ldcg(reinterpret_cast<const uint4*>(a.flow_succ) + 2 * (size_t)m + 1);
-  sc[0] = s03.x;
-  sc[1] = s03.y;
-  sc[2] = s03.z;
-  sc[3] = s03.w;
-  sc[4] = s47.x;
-  sc[5] = s47.y;
-  commit_move(a, R, rep, slot, c, pr);
-  flow_release(a, fb, out, sc);
+      for (int s = 0; s < 6; ++s) pr[s] = (s <= wl) ? __ldcg(&R.rec[c[s]]) : REC_OCC;
+      commit_move(a, R, rep, slot, c, pr);
+    }
+    fence_acq_rel();
+    const uint32_t sc[6] = {s03.x, s03.y, s03.z, s03.w, s47.x, s47.y};
+    m = flow_release(a, fb, out, sc);
+  }
 }
 
 // Moves every entry of list `in` (shared memory, n entries) and then the
@@ -134,7 +167,7 @@ __device__ __forceinline__ uint32_t flow_rounds(const StepArgs& a, const PathTab
     const uint32_t n = min(fb.cnt[in], fb.qcap);
     if (n == 0u) break;
     for (uint32_t k = threadIdx.x; k < n; k += blockDim.x)
-      flow_move_released(a, tab, fb, in ^ 1, fb.list[in][k]);
+      flow_move_chain(a, tab, fb, in ^ 1, fb.list[in][k], limit);
     __syncthreads();  // every read of list `in` is done
     if (threadIdx.x == 0) fb.cnt[in] = 0u;
     in ^= 1;
@@ -149,7 +182,7 @@ __device__ __forceinline__ uint32_t flow_rounds(const StepArgs& a, const PathTab
 __global__ void __launch_bounds__(kMoveThreads, 2) k_move_flow(StepArgs a) {
   extern __shared__ __align__(16) unsigned char dsm[];
   __shared__ PathTab tab;
-  __shared__ uint32_t s_cnt[2], s_ovf;
+  __shared__ uint32_t s_cnt[2], s_ovf, s_rel;
   build_path_tab(&tab);
   Ctl* ctl = a.ctl;
   const uint32_t E = flow_epoch(ctl);
@@ -160,6 +193,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_flow(StepArgs a) {
   fb.list[1] = fb.list[0] + kFlowQ;
   fb.cnt = s_cnt;
   fb.ovf = &s_ovf;
+  fb.rel = &s_rel;
   const uint32_t qc = __ldcg(&ctl->flow_qcap);
   fb.qcap = (qc == 0u || qc > (uint32_t)kFlowQ) ? (uint32_t)kFlowQ : qc;
   // the step's movers go to the blocks in turn, kDeal at a time: the block's
@@ -169,12 +203,9 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_flow(StepArgs a) {
   if (n0 % kDeal && nch && (nch - 1) % G == b) nb -= kDeal - n0 % kDeal;
   auto mover_at = [&](uint32_t k) { return ((k / kDeal) * G + b) * kDeal + k % kDeal; };
   if (tid < 2) s_cnt[tid] = 0u;
-  if (tid == 0) s_ovf = 0u;
+  if (tid == 0) s_ovf = s_rel = 0u;
   const unsigned long long t_start = global_ns();
-  if (b == 0 && tid == 0) {
-    ctl->round_ns[0] = t_start;
-    for (int i = 0; i < 8; ++i) ctl->phase_ns[i] = 0ull;
-  }
+  if (b == 0 && tid == 0) ctl->round_ns[0] = t_start;
   __syncthreads();
 
   // ---- pass 1: one node per footprint cell, pushed onto the cell's list
@@ -204,12 +235,12 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_flow(StepArgs a) {
 
   // ---- pass 2: predecessors and successors on every footprint cell; the
   // lists of a mover's cells are walked side by side
-  uint32_t released_first = 0;
+  uint32_t n_first = 0, walk_max = 0;
+  unsigned long long walk_sum = 0ull;
   for (uint32_t k = tid; k < nb; k += blockDim.x) {
     const uint32_t m = mover_at(k);
     const MoveEntry e = a.act[2][m];
-    const int rep = (int)(e.ref >> 24), slot = (int)(e.ref & 0xFFFFFFu);
-    const RepDev& R = a.reps[rep];
+    const RepDev& R = a.reps[e.ref >> 24];
     int c[6], q[6];
     foot_cells(&tab, e.c0, R, e.info, c, q);
     const int n = (int)(e.info & MV_LEN);
@@ -245,7 +276,9 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_flow(StepArgs a) {
           }
           cur[s] = (uint32_t)nv[s];
           any = any || cur[s] != kEnd;
+          ++walk_sum;
         }
+      walk_max = max(walk_max, (uint32_t)it + 1u);
       if (!any) break;
       if (it >= kMaxWalk) {
         atomicCAS(&ctl->err, 0, kDevErrFlow);
@@ -255,26 +288,16 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_flow(StepArgs a) {
     uint32_t sc[6];
 #pragma unroll
     for (int s = 0; s < 6; ++s) sc[s] = sn[s] != kEnd ? sn[s] / 6u : kEnd;
+    const int d = __popc(pred);
+    // successors and d (word 6), published by the fence before the counter
+    // can reach zero
     uint4* sd = reinterpret_cast<uint4*>(a.flow_succ) + 2 * (size_t)m;
     __stcg(sd, make_uint4(sc[0], sc[1], sc[2], sc[3]));
-    __stcg(sd + 1, make_uint4(sc[4], sc[5], kEnd, kEnd));
-    const int d = __popc(pred);
-    // the addition releases the successor list to whoever ends up owning m
-    const int old = atom_add_acqrel(&a.flow_cnt[m], d);
-    if (old + d == 0) {
-      if (d == 0) {
-        commit_first(a, R, rep, slot, c, e.info);
-      } else {
-        const int wl = walk_len(e.info);
-        uint32_t pr[6];
-#pragma unroll
-        for (int s = 0; s < 6; ++s) pr[s] = (s <= wl) ? __ldcg(&R.rec[c[s]]) : REC_OCC;
-        commit_move(a, R, rep, slot, c, pr);
-      }
-      flow_release(a, fb, 0, sc);
-    } else {
-      ++released_first;
-    }
+    __stcg(sd + 1, make_uint4(sc[4], sc[5], (uint32_t)d, kEnd));
+    fence_acq_rel();
+    const int old = atomicAdd(&a.flow_cnt[m], d);
+    if (old + d == 0) flow_enqueue(a, fb, 0, m);  // no predecessors, or all have moved
+    n_first += d == 0;
   }
   if (tid == 0) atomicMax(&ctl->phase_ns[2], global_ns() - t_start);
 
@@ -299,7 +322,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_flow(StepArgs a) {
     }
     __syncthreads();
     for (uint32_t i = lo + tid; i < hi; i += blockDim.x)
-      flow_move_released(a, &tab, fb, 0, __ldcg(&a.flow_ovf[i]));
+      flow_move_chain(a, &tab, fb, 0, __ldcg(&a.flow_ovf[i]), n0 + 1u);
     rounds += flow_rounds(a, &tab, fb, 0, n0 + 1u);
     ++waves;
     if (waves > n0 + 1u) {
@@ -307,11 +330,23 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_flow(StepArgs a) {
       return;
     }
   }
+  // statistics of the step (sums and maxima over the threads and blocks)
+  for (int o = 16; o > 0; o >>= 1) {
+    walk_max = max(walk_max, __shfl_xor_sync(0xffffffffu, walk_max, o));
+    walk_sum += __shfl_xor_sync(0xffffffffu, walk_sum, o);
+    n_first += __shfl_xor_sync(0xffffffffu, n_first, o);
+  }
+  if ((tid & 31) == 0) {
+    atomicMax(&ctl->flow_stat[0], (unsigned long long)walk_max);
+    atomicAdd(&ctl->flow_stat[1], walk_sum);
+    atomicAdd(&ctl->flow_stat[2], (unsigned long long)n_first);
+  }
   if (tid == 0) {
-    atomicMax(&ctl->phase_ns[4], (unsigned long long)nb);
-    atomicMax(&ctl->phase_ns[5], (unsigned long long)released_first);
+    atomicAdd(&ctl->flow_stat[3], (unsigned long long)s_rel);
+    atomicMax(&ctl->flow_stat[4], (unsigned long long)nb);
+    atomicMax(&ctl->flow_stat[5], (unsigned long long)s_rel);
     atomicMax(&ctl->phase_ns[7], (unsigned long long)rounds);
-    atomicMax((unsigned int*)&ctl->rounds_last, rounds + waves + 1u);
+    atomicMax((unsigned int*)&ctl->rounds_last, rounds + waves + 2u);
   }
   if (b == 0 && tid == 0) {
     // every block has read the pass's tag (the last barrier is behind them)

@@ -282,10 +282,10 @@ def test_claim_tag_cleanups(fg, orc, reserve, tag):
 
 @pytest.mark.parametrize("options", [
     dict(move_schedule=0),                      # rounds of claims, a grid barrier each
-    dict(move_schedule=1),                      # the dataflow schedule (default)
-    dict(flow_list_cap=1),                      # nearly every release spills: waves
-    dict(flow_list_cap=7),
-    dict(flow_tag=0xFFFFFF00 - 3),              # list-head tags restart within the run
+    dict(move_schedule=1),                      # the dataflow schedule
+    dict(move_schedule=1, flow_list_cap=1),     # nearly every release spills: waves
+    dict(move_schedule=1, flow_list_cap=7),
+    dict(move_schedule=1, flow_tag=0xFFFFFF00 - 3),   # list-head tags restart
 ])
 def test_move_schedules(fg, orc, options):
     """Both schedules of the sequential movement, the dataflow schedule with

@@ -289,20 +289,20 @@ def footprints(t, cells, desired):
 
 
 def dataflow_schedule(t, cells, desired, prio, rng, succ_rule="next", foot_mode="exact"):
-    """The dataflow schedule of the movement kernel, with its operations
-    interleaved in a random order as concurrent threads may run them.
+    """The dataflow schedule of the movement kernel, with its concurrent
+    operations interleaved in a random order.
 
     Every mover joins the list of each footprint cell (push order random);
     it counts the cells on which some mover comes before it (d) and notes,
-    per cell, the mover right after it (its successor).  Counters start at 0;
-    the pending operations are every mover's "+d" and, once a mover has
+    per cell, the mover right after it (its successor).  Counters start at
+    0; the pending operations are every mover's "+d" and, once a mover has
     moved, one "-1" per successor; whichever operation leaves a counter at 0
     moves that mover.  A mover with d = 0 applies the walk computed from the
     occupancy at the start of the movement (as the movement-order pass
     records it); the others walk against the occupancy of the moment.
     Returns the final cells and the number of times each mover moved.
-    succ_rule="last" (the last mover on the cell instead of the next one) and
-    foot_mode="no_start" are planted mistakes."""
+    succ_rule="last" (the last mover on the cell instead of the next one)
+    and foot_mode="no_start" are planted mistakes."""
     flat = t.ravel()
     cell = [int(c) for c in cells]
     paths, foot = footprints(t, cells, desired)
