@@ -52,8 +52,7 @@ KERNEL_SOURCES = {
     "k_plan_tile": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
     "k_plan_fp32": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
     "k_plan_direct": ["plan_kernels.cuh", "fast_device.cuh", "fast_internal.h"],
-    "k_move_rounds": ["move.cu", "move_common.cuh", "fast_device.cuh", "fast_internal.h"],
-    "k_move_flow": ["move_flow.cu", "move_common.cuh", "fast_device.cuh", "fast_internal.h"],
+    "k_move_rounds": ["move.cu", "fast_device.cuh", "fast_internal.h"],
 }
 
 
@@ -103,8 +102,6 @@ def parse():
                    help="v_m of the room and corridors workloads (default 4)")
     p.add_argument("--fp64-steps", type=int, default=None,
                    help="steps of the all-FP64 form timed (default: --steps)")
-    p.add_argument("--move-schedule", default="rounds", choices=["flow", "rounds"],
-                   help="GPU schedule of the sequential movement (same results)")
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -345,8 +342,7 @@ def bench_ours(args):
     n0 = [int(len(w.cells)) for w in works]
     mask_words = [1 if w.v_m <= 4 else 2 for w in works]
     fp64_steps = args.fp64_steps if args.fp64_steps is not None else args.steps
-    flow = args.move_schedule == "flow"
-    move_kernel = "k_move_flow" if flow else "k_move_rounds"
+    move_kernel = "k_move_rounds"
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     loop_graph = args.workload == "batch"
@@ -389,7 +385,6 @@ def bench_ours(args):
 
     def make_ctx(precision):
         ctx = fg.Context(n_rep, precision)
-        ctx.set_option("move_schedule", 1 if flow else 0)
         for r, w in enumerate(works):
             ctx.init_grid(r, w.cell_type, w.k_S, w.v_m, w.seed)
             ctx.place(r, w.cells)
@@ -432,7 +427,6 @@ def bench_ours(args):
     mv_wait, mv_us = ctx.move_profile()
     ctx_phases = list(ctx.last_move_phases)
     ctx_block_max = list(ctx.last_move_block_max)
-    ctx_flow_stats = list(ctx.last_flow_stats)
     al1 = alive_now(ctx)
     b1 = union_bytes(ctx, al1)
     u1 = union_cells(ctx)
@@ -545,22 +539,12 @@ def bench_ours(args):
                "sample": c["sample"], "choices_per_s": c["choices_per_s"]}
 
     ph = ctx_phases
-    if flow:
-        fs = ctx_flow_stats
-        move_last = {"phase_end_us": {k: round(ph[i] / 1e3, 2) for i, k in enumerate(
-                         ("list_pushes", "barrier", "list_walks", "block_rounds"))},
-                     "overflow_waves": int(ph[6]), "block_rounds_max": int(ph[7]),
-                     "longest_list": int(fs[0]), "list_nodes_walked": int(fs[1]),
-                     "movers_without_predecessor": int(fs[2]), "movers_released": int(fs[3]),
-                     "movers_per_block_max": int(fs[4]), "released_per_block_max": int(fs[5]),
-                     "times": "max over blocks, from the kernel's start"}
-    else:
-        move_last = {"waiting_after_round": [int(x) for x in mv_wait[:12]],
-                     "round_us": [round(float(x), 2) for x in mv_us[:12]],
-                     "waiting_max_block_after_round": [int(x) for x in ctx_block_max[:12]],
-                     "rounds": int(len(mv_wait)),
-                     "phases_max_over_blocks": [round(float(x) / 1e3, 2) if i not in (4, 5, 6)
-                                                else int(x) for i, x in enumerate(ph)]}
+    move_last = {"waiting_after_round": [int(x) for x in mv_wait[:12]],
+                 "round_us": [round(float(x), 2) for x in mv_us[:12]],
+                 "waiting_max_block_after_round": [int(x) for x in ctx_block_max[:12]],
+                 "rounds": int(len(mv_wait)),
+                 "phases_max_over_blocks": [round(float(x) / 1e3, 2) if i not in (4, 5, 6)
+                                            else int(x) for i, x in enumerate(ph)]}
     if rank == 0:
         cfg = workload_config(works, args.workload)
         cfg.update({"precision": "fp32 weights + fp64 re-check",
@@ -598,7 +582,6 @@ def bench_ours(args):
             "movers_per_step": movers,
             "rechecked_per_step": rechecked,
             "tile_fallback_warps_per_step": fallbacks,
-            "move_schedule": args.move_schedule,
             "move_rounds_per_step": rounds_per_step,
             "move_last_step": move_last,
             "roofline": {"bound": "hbm", "kernel": move_kernel, "achieved": achieved_move,

@@ -92,19 +92,6 @@ extern "C" {
 #define FAST_OPT_CLAIM_TAG 16     /* clears the claims and sets the next step's     */
                                   /* first claim tag, 0..254: a test hook for the   */
                                   /* clean-ups; results do not depend on it         */
-#define FAST_OPT_MOVE_SCHEDULE 17 /* how the sequential movement runs on the GPU    */
-                                  /* (same result either way): 0 (default) rounds   */
-                                  /* of claims, one grid barrier per round; 1 a     */
-                                  /* dataflow over the conflict graph, one grid     */
-                                  /* barrier per step                               */
-#define FAST_OPT_FLOW_LIST_CAP 18 /* dataflow schedule: released movers a block     */
-                                  /* keeps in shared memory per round, 1..8192     */
-                                  /* (0: 8192); more spill into a global list that  */
-                                  /* all blocks share after a grid barrier.  A test */
-                                  /* hook; results do not depend on it              */
-#define FAST_OPT_FLOW_TAG 19      /* dataflow schedule: tag of the last pass's list */
-                                  /* heads, 0..0xFFFFFF00 (there the heads are      */
-                                  /* cleared and the tags restart): a test hook    */
 
 typedef struct fast_ctx fast_ctx;
 
@@ -159,6 +146,8 @@ typedef struct {
   int64_t flips_unflagged; /* of those, outside the margin (must be 0)          */
   double max_abs_dp;       /* max |P32(k) - P64(k)| over cumulative probabilities */
   double margin;           /* relative margin M of the FP32 decision           */
+  int64_t flips_after_recheck; /* choices of the FP32 pass with the FP64 re-check */
+                           /* != FP64 rule (must be 0)                          */
 } fast_precision_report;
 
 typedef struct {
@@ -277,19 +266,13 @@ int fast_phase_times(fast_ctx* ctx, float* ms5);
  * per block still waiting after the first round, the round from which one
  * block finished alone (0: none), 0.  With max_rounds >= 137, t_ns[73 + r]
  * also receives the most movers still waiting in one block after round r,
- * for the rounds written.  With max_rounds >= 143, t_ns[137..142] receive
- * the dataflow schedule's counts of the step: the longest list walked, the
- * list nodes all walks visited, the movers without predecessors, the movers
- * released by a predecessor, the most movers of one block, the most movers
- * released to one block.  The dataflow schedule's phase times (t_ns[65..72],
- * max over blocks, ns from the kernel's start) are: list pushes done, grid
- * barrier passed, list walks done, the block's own rounds done (t_ns[69..70]
- * unused); then the overflow waves and the most rounds of one block
- * (counts). */
+ * for the rounds written. */
 int fast_move_profile(fast_ctx* ctx, int32_t max_rounds, uint32_t* n_wait, uint64_t* t_ns);
 
-/* Runs the FP32 planning of the current state without re-check next to the
- * FP64 rule and compares them (does not change the state).  Errors:
+/* Runs, on the current state, the planning pass (FP32 weights with the FP64
+ * re-check), the FP32 planning without re-check and the FP64 rule, and
+ * compares them.  Agents' cells and the step index do not change; the
+ * desired cells read back afterwards are this pass's.  Errors:
  * FAST_ESTATE (precision is FAST_FP64 or no agents), FAST_ENOMEM, FAST_ECUDA. */
 int fast_precision_report_run(fast_ctx* ctx, fast_precision_report* out);
 

@@ -23,8 +23,7 @@ PRECISION = {"fp64": 0, "fp32_recheck": 1, "fp32_norecheck": 2}
 REACH = {"l2": 0, "l2p": 1, "linf": 2}
 OPT = {"resort_period": 1, "digests": 2, "lanes_v1": 3, "lanes_v2": 4, "lanes_v3": 5,
        "lanes_v4": 6, "lanes_v5": 7, "barrier_ns": 10, "use_graph": 11, "move_blocks": 12,
-       "tile_shift": 13, "graph_steps": 14, "claim_reserve": 15, "claim_tag": 16,
-       "move_schedule": 17, "flow_list_cap": 18, "flow_tag": 19}
+       "tile_shift": 13, "graph_steps": 14, "claim_reserve": 15, "claim_tag": 16}
 ERRORS = {0: "FAST_OK", -1: "FAST_EINVAL", -2: "FAST_ESTATE", -3: "FAST_ENOMEM",
           -4: "FAST_ECUDA", -5: "FAST_ETIMEOUT"}
 
@@ -54,7 +53,8 @@ class Stats(C.Structure):
 
 class PrecisionReport(C.Structure):
     _fields_ = [("agents", C.c_int64), ("flagged", C.c_int64), ("flips", C.c_int64),
-                ("flips_unflagged", C.c_int64), ("max_abs_dp", C.c_double), ("margin", C.c_double)]
+                ("flips_unflagged", C.c_int64), ("max_abs_dp", C.c_double), ("margin", C.c_double),
+                ("flips_after_recheck", C.c_int64)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -303,13 +303,12 @@ class Context:
 
     def move_profile(self):
         """(waiting agents after each round's claims, round durations in us) of the last step."""
-        n_wait = np.zeros(150, np.uint32)
-        t_ns = np.zeros(150, np.uint64)
-        r = self._check(self.lib.fast_move_profile(self.h, 143, _ptr(n_wait), _ptr(t_ns)),
+        n_wait = np.zeros(140, np.uint32)
+        t_ns = np.zeros(140, np.uint64)
+        r = self._check(self.lib.fast_move_profile(self.h, 137, _ptr(n_wait), _ptr(t_ns)),
                         "fast_move_profile")
         m = min(r, 64)
         self.last_move_phases = t_ns[65:73].astype(np.float64).copy()
-        self.last_flow_stats = t_ns[137:143].astype(np.int64).copy()
         self.last_move_block_max = t_ns[73:73 + m].astype(np.int64).copy()
         return n_wait[:m].copy(), np.diff(t_ns[:m + 1].astype(np.float64)) / 1e3
 

@@ -21,7 +21,7 @@ LIB = os.path.join(OUT_DIR, "libfastgb.so")
 OBJ_DIR = os.path.join(HERE, "_build")
 
 SOURCES = ["plan.cu", "plan_v1.cu", "plan_v2.cu", "plan_v3.cu", "plan_v4.cu", "plan_v5.cu",
-           "move.cu", "move_flow.cu", "aux.cu", "noalloc.cu", "api.cpp", "floor_field.cpp"]
+           "move.cu", "aux.cu", "noalloc.cu", "api.cpp", "floor_field.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

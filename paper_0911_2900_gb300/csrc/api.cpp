@@ -81,10 +81,6 @@ struct fast_ctx {
   MoveEntry* d_act[3] = {nullptr, nullptr, nullptr};
   uint32_t* d_mv_prio = nullptr;
   uint32_t* d_mv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  unsigned long long* d_flow_node = nullptr;  // dataflow schedule, per mover slot
-  uint32_t* d_flow_succ = nullptr;
-  int32_t* d_flow_cnt = nullptr;
-  uint32_t* d_flow_ovf = nullptr;
 
   uint32_t list_cap = 0;
   uint32_t* d_bucket = nullptr;
@@ -137,7 +133,6 @@ struct fast_ctx {
   int move_blocks = 0;
   int tile_shift = 4;
   int graph_steps = 512;  // longest step loop captured as one graph
-  int move_schedule = MOVE_ROUNDS;
   bool resort_pending = false;  // agents placed since the last spatial sort
 
   int64_t t_host = 0;
@@ -371,10 +366,6 @@ int rebuild_layout(fast_ctx* c) {
     dfree(c, c->d_act[0]);
     dfree(c, c->d_mv_prio);
     for (auto& p : c->d_mv) dfree(c, p);
-    dfree(c, c->d_flow_node);
-    dfree(c, c->d_flow_succ);
-    dfree(c, c->d_flow_cnt);
-    dfree(c, c->d_flow_ovf);
     const size_t n = (size_t)total_cap;
     if (int e = alloc_into(c, &c->d_queue, n)) return e;
     if (int e = alloc_into(c, &c->d_act[2], n)) return e;
@@ -382,10 +373,6 @@ int rebuild_layout(fast_ctx* c) {
     if (int e = alloc_into(c, &c->d_mv_prio, n)) return e;
     for (auto& p : c->d_mv)
       if (int e = alloc_into(c, &p, n)) return e;
-    if (int e = alloc_into(c, &c->d_flow_node, 6 * n)) return e;
-    if (int e = alloc_into(c, &c->d_flow_succ, 8 * n)) return e;
-    if (int e = alloc_into(c, &c->d_flow_cnt, n)) return e;
-    if (int e = alloc_into(c, &c->d_flow_ovf, n)) return e;
     c->list_cap = (uint32_t)total_cap;
   }
   // bucket offsets, 2 words per replicate, the scan's block sums (<= 1024)
@@ -420,10 +407,6 @@ StepArgs args_of(fast_ctx* c) {
   a.mv_ref = c->d_mv[1];
   a.mv_info = c->d_mv[2];
   a.act_cap = c->list_cap;
-  a.flow_node = c->d_flow_node;
-  a.flow_succ = c->d_flow_succ;
-  a.flow_cnt = c->d_flow_cnt;
-  a.flow_ovf = c->d_flow_ovf;
   a.dig_cell = c->d_dig_cell;
   a.dig_des = c->d_dig_des;
   a.dig_cap = c->dig_cap;
@@ -440,9 +423,7 @@ int plan_grid(fast_ctx* c, int n_chunks) { return std::max(1, std::min(n_chunks,
 // (the rounds are latency-bound), capped by the work and by the option.
 int move_grid(fast_ctx* c) {
   int g = 0;
-  const int rc = c->move_schedule == MOVE_FLOW ? move_flow_max_grid(kMoveThreads, &g)
-                                               : move_rounds_max_grid(kMoveThreads, &g);
-  if (rc != 0 || g <= 0) g = c->sms;
+  if (move_rounds_max_grid(kMoveThreads, &g) != 0 || g <= 0) g = c->sms;
   if (c->move_blocks > 0) g = std::min(g, c->move_blocks);
   return std::max(g, 1);
 }
@@ -481,12 +462,7 @@ int enqueue_step(fast_ctx* c, bool resort) {
   if (c->digests) LAUNCH_TRY(c, digest_des_launch(a, all, plan_grid(c, all.n), c->cur));
   LAUNCH_TRY(c, move_prep_launch(a, all, plan_grid(c, all.n), c->cur));
   CUDA_TRY(c, record_event(c, 3));
-  if (c->move_schedule == MOVE_FLOW) {
-    LAUNCH_TRY(c, move_flow_launch(a, move_grid(c), kMoveThreads, c->cur));
-    c->launches += 1;  // move_flow_launch queues two kernels
-  } else {
-    LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), kMoveThreads, c->cur));
-  }
+  LAUNCH_TRY(c, move_rounds_launch(a, move_grid(c), kMoveThreads, c->cur));
   CUDA_TRY(c, record_event(c, 4));
   if (c->digests) {
     LAUNCH_TRY(c, digest_cell_launch(a, all, plan_grid(c, all.n), c->cur));
@@ -729,9 +705,7 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   R.speed_set = 0;
   for (auto& p : R.d.claim) dfree(c, p);
   dfree(c, R.d.cmark);
-  dfree(c, R.d.head);
   R.d.cmark = nullptr;
-  R.d.head = nullptr;
   R.d.rec = nullptr;
   R.d.mask = nullptr;
   R.d.claim[0] = R.d.claim[1] = nullptr;
@@ -748,7 +722,6 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   for (auto& p : R.d.claim)
     if (int e = alloc_into(c, &p, claim_cells)) return e;
   if (int e = alloc_into(c, &R.d.cmark, claim_cells)) return e;
-  if (int e = alloc_into(c, &R.d.head, claim_cells)) return e;
   RepDev& d = R.d;
   d.W = R.W;
   d.H = R.H;
@@ -767,7 +740,6 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   d.claim_tx = (R.W + 15) / 16;
   for (auto p : d.claim) CUDA_TRY(c, cudaMemsetAsync(p, 0xFF, claim_cells * 4, c->stream));
   CUDA_TRY(c, cudaMemsetAsync(d.cmark, 0, claim_cells, c->stream));
-  CUDA_TRY(c, cudaMemsetAsync(d.head, 0, claim_cells * 8, c->stream));
   R.grid_set = true;
   R.placed = false;
   R.n = 0;
@@ -1387,8 +1359,6 @@ int fast_move_profile(fast_ctx* c, int32_t max_rounds, uint32_t* n_wait, uint64_
     for (int i = 0; i < 8; ++i) t_ns[65 + i] = h.phase_ns[i];
   if (t_ns && max_rounds >= 64 + 1 + 8 + 64)
     for (int i = 0; i < n; ++i) t_ns[73 + i] = h.round_bmax[i];
-  if (t_ns && max_rounds >= 64 + 1 + 8 + 64 + 6)
-    for (int i = 0; i < 6; ++i) t_ns[137 + i] = h.flow_stat[i];
   return h.rounds_last;
 }
 
@@ -1425,12 +1395,22 @@ int fast_precision_report_run(fast_ctx* c, fast_precision_report* out) {
   const unsigned int zi = 0;
   CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->flips, z, 24, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->max_dp_bits, &zi, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->flips_after, &zi, 4, cudaMemcpyHostToDevice, c->stream));
   StepArgs a = args_of(c);
-  a.diag_p32 = p32;
-  a.diag_choice32 = ch32;
-  a.diag_flag = fl;
-  a.diag_base = db;
-  if (int e = enqueue_plan(c, a, true, false)) return e;
+  // the FP32 pass without re-check that records its choices, flags and
+  // cumulative probabilities (it writes its own choice into every desired
+  // cell), then the real planning pass (FP32 weights, FP64 re-check inside
+  // the margin), whose choices the comparison reads from the desired cells
+  LAUNCH_TRY(c, step_begin_launch(a, c->stream));
+  StepArgs ad = a;
+  ad.diag_p32 = p32;
+  ad.diag_choice32 = ch32;
+  ad.diag_flag = fl;
+  ad.diag_base = db;
+  if (int e = enqueue_plan(c, ad, true, false)) return e;
+  LAUNCH_TRY(c, step_begin_launch(a, c->stream));
+  if (int e = enqueue_plan(c, a, false, false)) return e;
+  a = ad;
   for (auto& g : c->groups) {
     Chunks ch{g.d_rep, g.d_begin, g.n};
     LAUNCH_TRY(c, plan_diag_compare_launch(a, g.v, c->reach, ch, plan_grid(c, g.n), c->stream));
@@ -1454,6 +1434,7 @@ int fast_precision_report_run(fast_ctx* c, fast_precision_report* out) {
   out->flagged = (int64_t)h.flagged;
   out->flips = (int64_t)h.flips;
   out->flips_unflagged = (int64_t)h.flips_unflagged;
+  out->flips_after_recheck = (int64_t)h.flips_after;
   float mdp;
   std::memcpy(&mdp, &h.max_dp_bits, 4);
   out->max_abs_dp = mdp;
@@ -1558,20 +1539,6 @@ int fast_set_option(fast_ctx* c, int32_t option, int64_t value) {
         CUDA_TRY(c, cudaMemsetAsync(R.d.cmark, 0, n, c->stream));
       }
       if (int e = write_ctl_int(c, offsetof(Ctl, claim_tag), (int32_t)value)) return e;
-      break;
-    case FAST_OPT_MOVE_SCHEDULE:
-      if (value != MOVE_ROUNDS && value != MOVE_FLOW)
-        return fail(c, FAST_EINVAL, "move schedule must be 0 (rounds) or 1 (dataflow)");
-      c->move_schedule = (int)value;
-      break;
-    case FAST_OPT_FLOW_LIST_CAP:
-      if (value < 0 || value > kFlowQ) return fail(c, FAST_EINVAL, "list capacity not in 0..%d", kFlowQ);
-      if (int e = write_ctl_int(c, offsetof(Ctl, flow_qcap), (int32_t)value)) return e;
-      break;
-    case FAST_OPT_FLOW_TAG:
-      if (value < 0 || value > (int64_t)kFlowEpochWrap)
-        return fail(c, FAST_EINVAL, "list tag not in 0..%u", kFlowEpochWrap);
-      if (int e = write_ctl_int(c, offsetof(Ctl, move_epoch), (int32_t)(uint32_t)value)) return e;
       break;
     case FAST_OPT_GRAPH_STEPS:
       if (value < 0 || value > 4096) return fail(c, FAST_EINVAL, "graph steps not in 0..4096");

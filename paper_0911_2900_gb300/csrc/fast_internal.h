@@ -19,10 +19,6 @@ constexpr int kDevErrRounds = 6;    // device error: movement rounds exceeded th
 constexpr int kRoundLog = 64;       // movement rounds recorded per step
 constexpr int kMoveThreads = 512;   // threads per block of the movement rounds (2 per SM)
 constexpr int kMoveSmemCap = 4500;  // movers per block kept in shared memory (24 B each)
-constexpr int kFlowQ = 8192;        // released movers one block of the dataflow schedule
-                                    // keeps per local round in shared memory (4 B each)
-constexpr uint32_t kFlowEpochWrap = 0xFFFFFF00u;  // list-head tags restart (heads cleared)
-enum { MOVE_ROUNDS = 0, MOVE_FLOW = 1 };  // schedules of the movement phase
 
 // One mover of the current step (16 bytes): start cell, (replicate << 24 |
 // slot), movement priority, footprint info.
@@ -51,8 +47,6 @@ struct RepDev {
                                     // tile-major (16x16-cell tiles of 1 KB)
   uint8_t* cmark;                   // same layout: stamp of the last step in which an
                                     // agent lost the cell's first-round claim
-  unsigned long long* head;         // same layout: dataflow schedule, head of the cell's
-                                    // list of movers (pass tag << 32 | node)
   int32_t* id;                      // [cap]
   int32_t* cell;                    // [cap]  -1: slot empty / agent left
   int32_t* desired;                 // [cap]
@@ -85,16 +79,7 @@ struct Ctl {
   uint32_t claim_tag;         // tag of the next step's first movement claims
   uint32_t tag_reserve;       // clear the claims before a step with fewer tags left
   uint32_t mark_stamp;        // this step's stamp for contested-cell marks (1..254)
-  uint32_t move_epoch;        // dataflow schedule: tag of the last pass's list heads
-  uint32_t flow_qcap;         // dataflow schedule: shared-memory list capacity (0: kFlowQ)
-  uint32_t ovf_count;         // dataflow schedule: released movers in the overflow list
-  uint32_t flow_waves;        // dataflow schedule: overflow waves of the last step
   uint32_t pad3;
-  // dataflow schedule, last step: [0] longest list walked, [1] list nodes
-  // visited by all walks, [2] movers without predecessors, [3] movers
-  // released by a predecessor, [4] most movers of one block, [5] most
-  // movers released to one block
-  unsigned long long flow_stat[6];
   unsigned long long rounds_total;
   unsigned long long rechecked_total;
   unsigned long long agent_steps;
@@ -103,7 +88,7 @@ struct Ctl {
   unsigned long long flips_unflagged;
   unsigned long long flagged;
   unsigned int max_dp_bits;          // float bits of max |p32 - p64|
-  unsigned int pad1;
+  unsigned int flips_after;          // choices of the FP32 + FP64 re-check pass != FP64 rule
   unsigned long long tile_fallbacks; // planning warps whose agents did not fit a tile
   unsigned long long movers_total;   // movers handed to the movement rounds, all steps
   unsigned long long foot_total;     // their footprint cells, all steps
@@ -139,14 +124,6 @@ struct StepArgs {
   uint32_t act_cap;
   // movement state when a block's movers do not fit its shared memory
   uint32_t *mv_prio, *mv_c0, *mv_ref, *mv_info, *mv_list[3];
-  // dataflow schedule of the movement: per mover m (index in act[2]) its
-  // list nodes node[6m + s] = priority << 32 | next node, its successors
-  // succ[8m + s] on footprint cell s (kEnd: none), its count of predecessors
-  // not yet moved, and the movers released beyond the shared-memory lists
-  unsigned long long* flow_node;  // [6 * act_cap]
-  uint32_t* flow_succ;            // [8 * act_cap]
-  int32_t* flow_cnt;              // [act_cap]
-  uint32_t* flow_ovf;             // [act_cap]
   unsigned long long* dig_cell;  // [dig_cap * n_rep] per-step digests (optional)
   unsigned long long* dig_des;
   int32_t dig_cap;
@@ -170,8 +147,6 @@ int plan_diag_compare_launch(const StepArgs& a, int v, int reach, const Chunks& 
 int move_prep_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s);
 int move_rounds_launch(const StepArgs& a, int grid, int block, cudaStream_t s);
 int move_rounds_max_grid(int block, int* grid_out);
-int move_flow_launch(const StepArgs& a, int grid, int block, cudaStream_t s);
-int move_flow_max_grid(int block, int* grid_out);
 int step_end_launch(const StepArgs& a, cudaStream_t s);
 int step_begin_launch(const StepArgs& a, cudaStream_t s);
 int digest_des_launch(const StepArgs& a, const Chunks& ch, int grid, cudaStream_t s);

@@ -572,6 +572,9 @@ __global__ void __launch_bounds__(128) k_diag_compare(StepArgs a, Chunks ch) {
         atomicAdd(&a.ctl->flips, 1ull);
         if (!flagged) atomicAdd(&a.ctl->flips_unflagged, 1ull);
       }
+      // the real planning pass (FP32 weights, FP64 re-check inside the
+      // margin) that ran before the diagnostic one left its choice here
+      if (R.desired[slot] != target) atomicAdd(&a.ctl->flips_after, 1u);
       const float* dp = a.diag_p32 + di * (int64_t)kMaxK;
       float mx = 0.f;
       for (int k = 0; k < K; ++k) mx = fmaxf(mx, (float)fabs((double)dp[k] - cum[k]));

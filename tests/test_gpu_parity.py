@@ -33,10 +33,8 @@ def fg():
 
 def run_gpu(fg, works, steps, precision="fp32_recheck", reach="l2", digests=True, resort=8,
             graph=True, id_perm=None, start_step=0, lanes=None, tile_shift=None, chunks=None,
-            graph_steps=None, tune=None, speeds=None, options=None):
+            graph_steps=None, tune=None, speeds=None):
     ctx = fg.Context(len(works), precision, reach)
-    for name, value in (options or {}).items():
-        ctx.set_option(name, value)
     ctx.set_option("digests", 1 if digests else 0)
     ctx.set_option("resort_period", resort)
     ctx.set_option("use_graph", 1 if graph else 0)
@@ -266,7 +264,6 @@ def test_claim_tag_cleanups(fg, orc, reserve, tag):
     steps = 20
     o = run_oracle(orc, w, steps)
     ctx = fg.Context(1, "fp32_recheck")
-    ctx.set_option("move_schedule", 0)
     ctx.set_option("digests", 1)
     ctx.set_option("claim_reserve", reserve)
     ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
@@ -280,19 +277,10 @@ def test_claim_tag_cleanups(fg, orc, reserve, tag):
     assert_same(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd), o, steps)
 
 
-@pytest.mark.parametrize("options", [
-    dict(move_schedule=0),                      # rounds of claims, a grid barrier each
-    dict(move_schedule=1),                      # the dataflow schedule
-    dict(move_schedule=1, flow_list_cap=1),     # nearly every release spills: waves
-    dict(move_schedule=1, flow_list_cap=7),
-    dict(move_schedule=1, flow_tag=0xFFFFFF00 - 3),   # list-head tags restart
-])
-def test_move_schedules(fg, orc, options):
-    """Both schedules of the sequential movement, the dataflow schedule with
-    shared-memory lists so small that released movers spill into the global
-    overflow list (and are moved in waves after grid barriers), and list-head
-    tags that run out and restart: the oracle's trajectories every time, on a
-    dense room (long priority chains) and a batch of replicates."""
+def test_dense_room_and_batch(fg, orc):
+    """A room four fifths full (long priority chains in the movement rounds)
+    next to a batch of replicates in one context: the oracle's trajectories
+    for every replicate."""
     t2 = wl.room(40, 32)
     wl.add_exit(t2, "left", 12, 3)
     wl.add_exit(t2, "top", 20, 2)
@@ -301,7 +289,7 @@ def test_move_schedules(fg, orc, options):
     dense = wl.Workload("dense", t2, cells.astype(np.int32), 5, seed=12)
     works = [dense] + wl.config_batch(n_rep=3, seed=17, cells_hi=200 ** 2, agents_hi=4000)
     steps = 40
-    _, gs = run_gpu(fg, works, steps, "fp32_recheck", options=options)
+    _, gs = run_gpu(fg, works, steps, "fp32_recheck")
     for w, g in zip(works, gs):
         assert_same(g, run_oracle(orc, w, steps), steps)
 
@@ -495,7 +483,7 @@ def test_precision_form_full_length(fg, orc):
     ctx.place(0, w.cells)
     ctx.autotune(trials=2)
     rep = ctx.precision_report()
-    assert rep["flips_unflagged"] == 0
+    assert rep["flips_unflagged"] == 0 and rep["flips_after_recheck"] == 0
     assert rep["flagged"] < 0.01 * rep["agents"]
     ctx.step(steps)
     cells, des, st = ctx.readback(0, len(w.cells))
@@ -517,7 +505,7 @@ def test_stress_form_from_start(fg, orc):
     ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
     ctx.place(0, w.cells)
     rep = ctx.precision_report()
-    assert rep["flips_unflagged"] == 0
+    assert rep["flips_unflagged"] == 0 and rep["flips_after_recheck"] == 0
     assert rep["flagged"] < 0.02 * rep["agents"]
     ctx.step(steps)
     cells, des, st = ctx.readback(0, len(w.cells))

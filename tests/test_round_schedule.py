@@ -257,132 +257,3 @@ def test_dropping_the_contested_cells_is_caught():
             got, _ = refined_schedule(t, cells, desired, prio, keep_contested=False)
             differ += not np.array_equal(got, sequential(t, cells, desired, v, seed, step))
     assert differ > 0
-
-
-# --------------------------------------------------------------------------- dataflow
-def footprints(t, cells, desired):
-    """Paths and footprints of the movers, as the movement-order pass finds
-    them (agents that stay, or are blocked at once, are not movers)."""
-    H, W = t.shape
-    flat = t.ravel()
-    cell = [int(c) for c in cells]
-    stays = {cell[i] for i in range(len(cells)) if desired[i] == cell[i]}
-    paths, foot = {}, {}
-    for i in range(len(cells)):
-        if desired[i] == cell[i]:
-            continue
-        x0, y0 = cell[i] % W, cell[i] // W
-        dx, dy = int(desired[i]) % W - x0, int(desired[i]) // W - y0
-        p = [(y0 + py) * W + (x0 + px) for px, py in oracle.path(dx, dy)]
-        fp, leaves = [], False
-        for c in p:
-            if flat[c] == WALL or c in stays:
-                break
-            if flat[c] == EXIT:
-                leaves = True
-                break
-            fp.append(c)
-        if fp or leaves:
-            foot[i] = [cell[i]] + fp
-            paths[i] = p
-    return paths, foot
-
-
-def dataflow_schedule(t, cells, desired, prio, rng, succ_rule="next", foot_mode="exact"):
-    """The dataflow schedule of the movement kernel, with its concurrent
-    operations interleaved in a random order.
-
-    Every mover joins the list of each footprint cell (push order random);
-    it counts the cells on which some mover comes before it (d) and notes,
-    per cell, the mover right after it (its successor).  Counters start at
-    0; the pending operations are every mover's "+d" and, once a mover has
-    moved, one "-1" per successor; whichever operation leaves a counter at 0
-    moves that mover.  A mover with d = 0 applies the walk computed from the
-    occupancy at the start of the movement (as the movement-order pass
-    records it); the others walk against the occupancy of the moment.
-    Returns the final cells and the number of times each mover moved.
-    succ_rule="last" (the last mover on the cell instead of the next one)
-    and foot_mode="no_start" are planted mistakes."""
-    flat = t.ravel()
-    cell = [int(c) for c in cells]
-    paths, foot = footprints(t, cells, desired)
-    if foot_mode == "no_start":
-        foot = {i: f[1:] for i, f in foot.items()}
-    occ0 = set(cell)
-
-    def walk(i, occ):
-        cur, gone = cell[i], False
-        for c in paths[i]:
-            if flat[c] == WALL or c in occ:
-                break
-            cur = c
-            if flat[c] == EXIT:
-                gone = True
-                break
-        return cur, gone
-
-    first = {i: walk(i, occ0) for i in foot}
-    lists = {}
-    order = list(foot)
-    rng.shuffle(order)
-    for i in order:
-        for c in foot[i]:
-            lists.setdefault(c, []).insert(0, i)   # a push onto the head
-    d, succ = {}, {}
-    for i in foot:
-        d[i], succ[i] = 0, []
-        for c in foot[i]:
-            before = [j for j in lists[c] if prio[j] < prio[i]]
-            after = [j for j in lists[c] if prio[j] > prio[i]]
-            d[i] += bool(before)
-            if after:
-                pick = min if succ_rule == "next" else max
-                succ[i].append(pick(after, key=lambda j: prio[j]))
-    occ = set(cell)
-    cnt = {i: 0 for i in foot}
-    moved = {i: 0 for i in foot}
-    pending = [("add", i) for i in foot]
-
-    def move(i):
-        cur, gone = first[i] if d[i] == 0 else walk(i, occ)
-        moved[i] += 1
-        if cur != cell[i] or gone:
-            occ.discard(cell[i])
-            if gone:
-                cell[i] = -1
-            else:
-                occ.add(cur)
-                cell[i] = cur
-        pending.extend(("sub", j) for j in succ[i])
-
-    while pending:
-        op, i = pending.pop(int(rng.integers(len(pending))))
-        cnt[i] += d[i] if op == "add" else -1
-        if cnt[i] == 0:
-            move(i)
-    return np.array(cell, np.int32), moved
-
-
-@pytest.mark.parametrize("v", [1, 2, 3, 4, 5])
-def test_dataflow_equals_the_sequential_loop(v):
-    rng = np.random.default_rng(7 + v)
-    for t, cells, desired, seed, step in scenes(v):
-        prio = [oracle.move_priority(seed, i, step) for i in range(len(cells))]
-        want = sequential(t, cells, desired, v, seed, step)
-        for _ in range(3):   # three interleavings of the concurrent operations
-            got, moved = dataflow_schedule(t, cells, desired, prio, rng)
-            assert set(moved.values()) <= {1}, "a mover moved twice or never"
-            assert np.array_equal(got, want)
-
-
-@pytest.mark.parametrize("mistake", [dict(succ_rule="last"), dict(foot_mode="no_start")])
-def test_comparison_catches_a_wrong_dataflow(mistake):
-    rng = np.random.default_rng(3)
-    differ = 0
-    for v in (2, 4, 5):
-        for t, cells, desired, seed, step in scenes(v):
-            prio = [oracle.move_priority(seed, i, step) for i in range(len(cells))]
-            got, moved = dataflow_schedule(t, cells, desired, prio, rng, **mistake)
-            differ += (not np.array_equal(got, sequential(t, cells, desired, v, seed, step))
-                       or set(moved.values()) != {1})
-    assert differ > 0
