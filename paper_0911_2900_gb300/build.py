@@ -53,7 +53,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     nvcc = _nvcc()
     os.makedirs(OUT_DIR, exist_ok=True)
     os.makedirs(OBJ_DIR, exist_ok=True)
-    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    # host code: no fused multiply-add contraction (the exact floor field's
+    # doubles are fl(a + fl(b * sqrt2)) on every host, x86 and Arm alike)
+    common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
+              "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
 
     def compile_one(src):
         obj = os.path.join(OBJ_DIR, src + ".o")
