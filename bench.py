@@ -66,8 +66,8 @@ def source_digest(kernel):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel, workload_name, profiles_dir=None):
-    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the
+def profile_field(kernel, workload_name, field, profiles_dir=None):
+    """A figure (dram_bytes_per_launch, warp_instructions_per_launch) of the
     committed ncu summary of this kernel on this workload, or None when there
     is none or the kernel's sources changed since it was taken."""
     path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"),
@@ -76,14 +76,36 @@ def measured_traffic(kernel, workload_name, profiles_dir=None):
         fields = {}
         with open(path) as fh:
             for ln in fh:
-                if ":" in ln and ln.split(":")[0] in ("source_digest", "dram_bytes_per_launch"):
+                if ":" in ln and ln.split(":")[0] in ("source_digest", field):
                     k, v = ln.split(":", 1)
                     fields[k] = v.strip()
         if fields.get("source_digest") != source_digest(kernel):
             return None
-        return float(fields["dram_bytes_per_launch"])
+        return float(fields[field])
     except (OSError, KeyError, ValueError):
         return None
+
+
+def measured_traffic(kernel, workload_name, profiles_dir=None):
+    """dram__bytes_read.sum + dram__bytes_write.sum per launch from the
+    committed ncu summary of this kernel on this workload (None: none, or
+    stale)."""
+    return profile_field(kernel, workload_name, "dram_bytes_per_launch", profiles_dir)
+
+
+def issue_ceiling(kernel, workload_name, measured_us, sm_mhz, sms):
+    """The kernel's time at 100 % instruction issue (its warp instructions
+    per launch from the committed ncu summary / (SMs x 4 schedulers x one
+    instruction per cycle x the sampled SM clock)) and the measured time's
+    fraction of it; None without a current summary."""
+    inst = profile_field(kernel, workload_name, "warp_instructions_per_launch")
+    if inst is None or not sm_mhz or not sms or not measured_us:
+        return None
+    peak = sms * 4 * sm_mhz * 1e6
+    min_us = inst / peak * 1e6
+    return {"warp_instructions_per_launch": inst, "issue_peak_warp_inst_per_s": peak,
+            "us_at_full_issue": min_us, "frac_of_issue_peak": min_us / measured_us,
+            "sm_mhz": sm_mhz}
 
 
 def parse():
@@ -344,6 +366,7 @@ def bench_ours(args):
     fp64_steps = args.fp64_steps if args.fp64_steps is not None else args.steps
     move_kernel = "k_move_rounds"
     stream = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     loop_graph = args.workload == "batch"
 
@@ -596,7 +619,10 @@ def bench_ours(args):
                               "traffic": measured_traffic(plan_kernel, label),
                               "peak_kind": peak_kind, "bytes_per_launch": bytes_plan,
                               "bytes_per_launch_separate_arrays": bytes_plan_sep,
-                              "frac_separate_arrays": achieved_sep / peak},
+                              "frac_separate_arrays": achieved_sep / peak,
+                              "issue": issue_ceiling(plan_kernel, label,
+                                                     1e3 * statistics.mean(plan_ms),
+                                                     clk.get("sm_mhz"), sms)},
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),

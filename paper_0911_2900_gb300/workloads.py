@@ -292,3 +292,16 @@ def tiny_room(W=12, H=10, n=12, seed=0, v_m=2, walls=(), exits=(("bottom", 4, 2)
     for side, pos, width in exits:
         add_exit(t, side, pos, width)
     return Workload(f"tiny{W}x{H}", t, place_uniform(t, n, seed), v_m, seed=seed)
+
+
+def config_fd_corridor(density: float, length=2000, width=20, seed=0, v_m=4) -> Workload:
+    """Straight corridor for the fundamental diagram: `length` x `width`
+    free cells between walls, closed at the left end, the whole right end an
+    exit; agents uniform at `density` (fraction of the free cells)."""
+    t = room(length + 2, width + 2)
+    add_exit(t, "right", 1, width)
+    free = int((t == FREE).sum())
+    n = max(1, int(round(density * free)))
+    rs = int(seed * 1009 + round(density * 1000))
+    return Workload(f"corridor{length}x{width}_d{density:.2f}_v{v_m}", t,
+                    place_uniform(t, n, rs), v_m, seed=rs)

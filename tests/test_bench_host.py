@@ -87,3 +87,19 @@ def test_measured_traffic_follows_the_source_digest(tmp_path):
         "source_digest: 0000000000000000\ndram_bytes_per_launch: 123456\n")
     assert bench.measured_traffic("k_plan_direct", "wl", str(tmp_path)) is None
     assert bench.measured_traffic("k_plan_direct", "missing", str(tmp_path)) is None
+
+
+def test_issue_ceiling_from_the_profile(tmp_path, monkeypatch):
+    import bench
+
+    p = tmp_path / "k_plan_direct_wl.md"
+    p.write_text(f"source_digest: {bench.source_digest('k_plan_direct')}\n"
+                 "warp_instructions_per_launch: 1216000\n")
+    real = bench.profile_field
+    monkeypatch.setattr(bench, "profile_field",
+                        lambda k, w, f, d=None: real(k, w, f, str(tmp_path)))
+    r = bench.issue_ceiling("k_plan_direct", "wl", 10.0, 2000.0, 152)
+    # 1,216,000 / (152 x 4 x 2e9 per s) = 1 us at full issue
+    assert abs(r["us_at_full_issue"] - 1.0) < 1e-9 and abs(r["frac_of_issue_peak"] - 0.1) < 1e-9
+    assert bench.issue_ceiling("k_plan_direct", "other", 10.0, 2000.0, 152) is None
+    assert bench.issue_ceiling("k_plan_direct", "wl", 10.0, None, 152) is None
