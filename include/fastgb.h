@@ -342,6 +342,11 @@ int fast_selftest_exp64(const double* x, double* y, int64_t n);
 int fast_selftest_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n);
 /* Largest relative error of the SFU 2^y over every float y in [lo, hi]. */
 int fast_selftest_ex2(float lo, float hi, double* max_rel_err);
+/* L2 read bandwidth (GB/s): `iters` passes of every SM reading a buffer of
+ * `bytes` (16-byte multiple, 4 KiB..1 GiB; small enough to stay in L2) at L2
+ * level, after two untimed passes; CUDA-event timed.  For the roofline of
+ * planning passes whose cell records stay in L2. */
+int fast_selftest_l2_read(int64_t bytes, int32_t iters, double* gb_per_s);
 /* Average time of the library's grid barrier: a cooperative kernel of
  * `blocks` x `threads` (all resident) runs `iters` barriers in a row.
  * Returns FAST_EINVAL if the grid cannot be co-resident. */

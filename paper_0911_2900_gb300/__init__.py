@@ -96,6 +96,7 @@ EXPORTS = {
     "fast_move_profile": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "fast_reach_union": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fast_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
+    "fast_selftest_l2_read": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p]),
     "fast_floor_field": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "fast_plan_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
@@ -438,6 +439,15 @@ def selftest_ex2(lo: float, hi: float) -> float:
     rc = lib.fast_selftest_ex2(C.c_float(lo), C.c_float(hi), C.byref(v))
     if rc:
         raise FastError(rc, "fast_selftest_ex2")
+    return v.value
+
+
+def selftest_l2_read(nbytes: int = 32 << 20, iters: int = 50) -> float:
+    """L2 read bandwidth in GB/s (a buffer of nbytes read iters times)."""
+    v = C.c_double()
+    rc = load().fast_selftest_l2_read(int(nbytes), int(iters), C.byref(v))
+    if rc:
+        raise FastError(rc, "fast_selftest_l2_read")
     return v.value
 
 

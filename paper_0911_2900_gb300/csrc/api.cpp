@@ -1675,6 +1675,45 @@ int fast_selftest_ex2(float lo, float hi, double* max_rel_err) {
   return rc;
 }
 
+int fast_selftest_l2_read(int64_t bytes, int32_t iters, double* gb_per_s) {
+  if (bytes < 4096 || bytes > ((int64_t)1 << 30) || (bytes & 15) || iters < 1 || iters > 10000 ||
+      !gb_per_s)
+    return FAST_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return FAST_ECUDA;
+  void* buf = nullptr;
+  unsigned int* sink = nullptr;
+  if (cudaMalloc(&buf, (size_t)bytes) != cudaSuccess) return FAST_ENOMEM;
+  if (cudaMalloc(&sink, 4) != cudaSuccess) {
+    cudaFree(buf);
+    return FAST_ENOMEM;
+  }
+  int rc = FAST_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaMemset(buf, 1, (size_t)bytes) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess)
+    rc = FAST_ECUDA;
+  float ms = 0.f;
+  if (rc == FAST_OK) {
+    test_l2_read_launch(buf, (size_t)bytes, 2, sink, sms * 4, 0);  // warm the L2
+    cudaEventRecord(e0, 0);
+    test_l2_read_launch(buf, (size_t)bytes, iters, sink, sms * 4, 0);
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+        cudaGetLastError() != cudaSuccess)
+      rc = FAST_ECUDA;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(buf);
+  cudaFree(sink);
+  if (rc != FAST_OK) return rc;
+  *gb_per_s = (double)bytes * iters / (ms * 1e-3) / 1e9;
+  return FAST_OK;
+}
+
 int fast_selftest_barrier_cost(int32_t blocks, int32_t threads, int32_t iters, double* ns_per_barrier) {
   if (blocks < 1 || threads < 32 || threads > 1024 || iters < 1 || !ns_per_barrier) return FAST_EINVAL;
   Ctl* d = nullptr;

@@ -519,4 +519,24 @@ int test_ex2_launch(float lo, float hi, unsigned long long* out, cudaStream_t s)
   return 0;
 }
 
+// L2 read bandwidth: every thread reads 16-byte words of a buffer that fits
+// in L2 at global (L2) level, `iters` passes; the xor of what it read keeps
+// the loads from being dropped.
+__global__ void k_test_l2_read(const uint4* buf, size_t n16, int iters, unsigned int* sink) {
+  uint32_t acc = 0u;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int it = 0; it < iters; ++it)
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n16; i += stride) {
+      const uint4 v = __ldcg(buf + i);
+      acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+  if (acc == 0x9E3779B9u) atomicAdd(sink, 1u);
+}
+
+int test_l2_read_launch(const void* buf, size_t bytes, int iters, unsigned int* sink, int grid,
+                        cudaStream_t s) {
+  k_test_l2_read<<<grid, 512, 0, s>>>(static_cast<const uint4*>(buf), bytes / 16, iters, sink);
+  return 0;
+}
+
 }  // namespace fastgb

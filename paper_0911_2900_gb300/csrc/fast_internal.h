@@ -173,6 +173,8 @@ int test_exp64_launch(const double* x, double* y, int64_t n, cudaStream_t s);
 int test_philox_launch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                        cudaStream_t s);
 int test_ex2_launch(float lo, float hi, unsigned long long* out_max_rel_bits, cudaStream_t s);
+int test_l2_read_launch(const void* buf, size_t bytes, int iters, unsigned int* sink, int grid,
+                        cudaStream_t s);
 int test_barrier_timeout_launch(Ctl* ctl, int grid, cudaStream_t s);
 int test_barrier_cost_launch(Ctl* ctl, int grid, int block, int iters, cudaStream_t s);
 int test_barrier_sum_launch(Ctl* ctl, int grid, int block, int iters, cudaStream_t s);
