@@ -342,6 +342,19 @@ int fast_selftest_exp64(const double* x, double* y, int64_t n);
 int fast_selftest_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n);
 /* Largest relative error of the SFU 2^y over every float y in [lo, hi]. */
 int fast_selftest_ex2(float lo, float hi, double* max_rel_err);
+/* 1 when this library is the debug build (FASTGB_CHECKED): its kernels check
+ * the indices they derive from data (agent and desired cells, candidate and
+ * path cells, mover and re-check queue entries) and turn one out of range
+ * into FAST_ECUDA at the next call that reads device errors, with the index
+ * in fast_last_error, instead of a memory access; 0 for the release build,
+ * which compiles the checks away. */
+int fast_build_checked(void);
+
+/* One index check of the debug build on the GPU (the index is used for no
+ * access): FAST_ECUDA with *recorded = index when it is outside [0, n), else
+ * FAST_OK with *recorded = -1; the release build always gives FAST_OK, -1. */
+int fast_selftest_bounds(int64_t index, int64_t n, int64_t* recorded);
+
 /* L2 read bandwidth (GB/s): `iters` passes of every SM reading a buffer of
  * `bytes` (16-byte multiple, 4 KiB..1 GiB; small enough to stay in L2) at L2
  * level, after two untimed passes; CUDA-event timed.  For the roofline of

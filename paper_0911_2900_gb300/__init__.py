@@ -97,6 +97,8 @@ EXPORTS = {
     "fast_reach_union": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "fast_set_option": (C.c_int, [C.c_void_p, C.c_int32, C.c_int64]),
     "fast_selftest_l2_read": (C.c_int, [C.c_int64, C.c_int32, C.c_void_p]),
+    "fast_build_checked": (C.c_int, []),
+    "fast_selftest_bounds": (C.c_int, [C.c_int64, C.c_int64, C.c_void_p]),
     "fast_floor_field": (C.c_int, [C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "fast_plan_noalloc": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_void_p]),
@@ -120,15 +122,20 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = True) -> C.CDLL:
-    """Loads libfastgb.so (building it first if it is missing or stale)."""
+    """Loads libfastgb.so (building it first if it is missing or stale); with
+    the environment variable FASTGB_CHECKED=1 the debug build, whose kernels
+    check the indices they derive from data (an index out of range becomes a
+    device error instead of a memory access)."""
     global _lib
     with _lock:
         if _lib is None:
+            checked = os.environ.get("FASTGB_CHECKED", "0") == "1"
+            path = _build.LIB_CHECKED if checked else _build.LIB
             if build_if_missing:
-                _build.build()
-            if not os.path.exists(_build.LIB):
-                raise FastError(-4, f"libfastgb.so not built ({_build.LIB})")
-            lib = C.CDLL(_build.LIB)
+                _build.build(checked=checked)
+            if not os.path.exists(path):
+                raise FastError(-4, f"{os.path.basename(path)} not built ({path})")
+            lib = C.CDLL(path)
             for name, (res, args) in EXPORTS.items():
                 f = getattr(lib, name)
                 f.restype = res
@@ -440,6 +447,20 @@ def selftest_ex2(lo: float, hi: float) -> float:
     if rc:
         raise FastError(rc, "fast_selftest_ex2")
     return v.value
+
+
+def build_checked() -> bool:
+    """True when the loaded library is the debug build with index checks."""
+    return load().fast_build_checked() == 1
+
+
+def selftest_bounds(index: int, n: int):
+    """(return code, index recorded) of one index check of the debug build
+    on the GPU: FAST_ECUDA and the index when it is outside [0, n); in the
+    release build the checks are compiled away (FAST_OK, -1)."""
+    v = C.c_int64(-1)
+    rc = load().fast_selftest_bounds(int(index), int(n), C.byref(v))
+    return rc, v.value
 
 
 def selftest_l2_read(nbytes: int = 32 << 20, iters: int = 50) -> float:

@@ -18,6 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "lib")
 LIB = os.path.join(OUT_DIR, "libfastgb.so")
+LIB_CHECKED = os.path.join(OUT_DIR, "libfastgb_checked.so")  # debug build: index checks
 OBJ_DIR = os.path.join(HERE, "_build")
 
 SOURCES = ["plan.cu", "plan_v1.cu", "plan_v2.cu", "plan_v3.cu", "plan_v4.cu", "plan_v5.cu",
@@ -40,26 +41,33 @@ def _inputs():
     return files
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _inputs())
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    if not force and up_to_date():
-        return LIB
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False,
+          checked: bool = False) -> str:
+    """Builds the release library, or with checked=True the debug build in
+    which kernels check the indices they derive from data (FASTGB_CHECKED)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and up_to_date(lib):
+        return lib
     nvcc = _nvcc()
+    obj_dir = OBJ_DIR + ("_checked" if checked else "")
     os.makedirs(OUT_DIR, exist_ok=True)
-    os.makedirs(OBJ_DIR, exist_ok=True)
+    os.makedirs(obj_dir, exist_ok=True)
     # host code: no fused multiply-add contraction (the exact floor field's
     # doubles are fl(a + fl(b * sqrt2)) on every host, x86 and Arm alike)
     common = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
               "-ffp-contract=off", "-I", INCLUDE, "-I", CSRC]
+    if checked:
+        common.append("-DFASTGB_CHECKED")
 
     def compile_one(src):
-        obj = os.path.join(OBJ_DIR, src + ".o")
+        obj = os.path.join(obj_dir, src + ".o")
         path = os.path.join(CSRC, src)
         if src.endswith(".cu"):
             cmd = [nvcc, *ARCH, *common, "-rdc=false", "-c", path, "-o", obj]
@@ -78,13 +86,13 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         for obj, log in results:
             if log.strip():
                 print(f"== {os.path.basename(obj)}\n{log}", file=sys.stderr)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

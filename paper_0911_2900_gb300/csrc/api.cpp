@@ -566,6 +566,9 @@ int check_device_error(fast_ctx* c) {
   if (h.err == kDevErrTimeout)
     return fail(c, FAST_ETIMEOUT, "a device-side wait exceeded its limit (%lld ns)",
                 (long long)c->barrier_ns);
+  if (h.err == kDevErrBounds)
+    return fail(c, FAST_ECUDA, "a kernel found index %lld out of range (debug build)",
+                (long long)h.bad_index);
   if (h.err != 0) return fail(c, FAST_ECUDA, "device error code %d", h.err);
   return FAST_OK;
 }
@@ -1673,6 +1676,30 @@ int fast_selftest_ex2(float lo, float hi, double* max_rel_err) {
   std::memcpy(&v, &h, 8);
   *max_rel_err = v;
   return rc;
+}
+
+int fast_build_checked(void) { return build_checked(); }
+
+int fast_selftest_bounds(int64_t index, int64_t n, int64_t* recorded) {
+  if (!recorded || n < 0) return FAST_EINVAL;
+  *recorded = -1;
+  Ctl* d = nullptr;
+  if (cudaMalloc(&d, sizeof(Ctl)) != cudaSuccess) return FAST_ENOMEM;
+  Ctl h{};
+  int rc = FAST_OK;
+  if (cudaMemcpy(d, &h, sizeof h, cudaMemcpyHostToDevice) != cudaSuccess) rc = FAST_ECUDA;
+  if (rc == FAST_OK) test_bounds_launch(d, (long long)index, (long long)n, 0);
+  if (rc == FAST_OK && (cudaDeviceSynchronize() != cudaSuccess || cudaGetLastError() != cudaSuccess))
+    rc = FAST_ECUDA;
+  if (rc == FAST_OK && cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost) != cudaSuccess)
+    rc = FAST_ECUDA;
+  cudaFree(d);
+  if (rc != FAST_OK) return rc;
+  if (h.err == kDevErrBounds) {
+    *recorded = h.bad_index;
+    return FAST_ECUDA;
+  }
+  return FAST_OK;
 }
 
 int fast_selftest_l2_read(int64_t bytes, int32_t iters, double* gb_per_s) {

@@ -519,6 +519,18 @@ int test_ex2_launch(float lo, float hi, unsigned long long* out, cudaStream_t s)
   return 0;
 }
 
+// One index check of the debug build (the index is not used for any access).
+__global__ void k_test_bounds(Ctl* ctl, long long index, long long n) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) (void)fg_in(ctl, index, n);
+}
+
+int test_bounds_launch(Ctl* ctl, long long index, long long n, cudaStream_t s) {
+  k_test_bounds<<<1, 32, 0, s>>>(ctl, index, n);
+  return 0;
+}
+
+int build_checked() { return kChecked ? 1 : 0; }
+
 // L2 read bandwidth: every thread reads 16-byte words of a buffer that fits
 // in L2 at global (L2) level, `iters` passes; the xor of what it read keeps
 // the loads from being dropped.

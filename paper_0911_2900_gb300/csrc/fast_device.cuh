@@ -30,6 +30,27 @@ __device__ __forceinline__ bool rec_sentinel(uint32_t r) {
 }
 
 // --------------------------------------------------------------------------
+// Debug build (compiled with FASTGB_CHECKED): the indices the step kernels
+// derive from data -- an agent's cell and desired cell, candidate and path
+// cells, mover and re-check queue entries -- are checked against the array
+// they index before use.  One out of range records kDevErrBounds and the
+// index in the control block, and the access is skipped (the agent is left
+// where it is); nothing traps.  The release build compiles the checks away.
+#ifdef FASTGB_CHECKED
+constexpr bool kChecked = true;
+static __device__ __noinline__ bool fg_bad_index(Ctl* ctl, long long i) {
+  if (atomicCAS(&ctl->err, 0, kDevErrBounds) == 0) ctl->bad_index = i;
+  return false;
+}
+__device__ __forceinline__ bool fg_in(Ctl* ctl, long long i, long long n) {
+  return (i >= 0 && i < n) ? true : fg_bad_index(ctl, i);
+}
+#else
+constexpr bool kChecked = false;
+__device__ __forceinline__ bool fg_in(Ctl*, long long, long long) { return true; }
+#endif
+
+// --------------------------------------------------------------------------
 // Reach sets (movement reach of one step): offsets (dx,dy) with
 // dx^2+dy^2 <= v^2 (L2), <= v^2+v (L2P) or max(|dx|,|dy|) <= v (LINF), listed
 // row by row (dy ascending, then dx ascending).

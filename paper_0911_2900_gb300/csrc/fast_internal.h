@@ -16,6 +16,7 @@ constexpr int kChunk = 256;         // agents per work chunk
 constexpr int kMaxK = 121;          // largest reach set (L-infinity, v_m = 5)
 constexpr int kDevErrTimeout = 5;   // device error: a bounded wait gave up
 constexpr int kDevErrRounds = 6;    // device error: movement rounds exceeded the bound
+constexpr int kDevErrBounds = 9;    // device error (debug build): an index out of range
 constexpr int kRoundLog = 64;       // movement rounds recorded per step
 constexpr int kMoveThreads = 512;   // threads per block of the movement rounds (2 per SM)
 constexpr int kMoveSmemCap = 4500;  // movers per block kept in shared memory (24 B each)
@@ -90,6 +91,7 @@ struct Ctl {
   unsigned int max_dp_bits;          // float bits of max |p32 - p64|
   unsigned int flips_after;          // choices of the FP32 + FP64 re-check pass != FP64 rule
   unsigned long long tile_fallbacks; // planning warps whose agents did not fit a tile
+  long long bad_index;               // debug build: the first index found out of range
   unsigned long long movers_total;   // movers handed to the movement rounds, all steps
   unsigned long long foot_total;     // their footprint cells, all steps
   // movement instrumentation of the last step: agents still waiting after
@@ -173,6 +175,8 @@ int test_exp64_launch(const double* x, double* y, int64_t n, cudaStream_t s);
 int test_philox_launch(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int64_t n,
                        cudaStream_t s);
 int test_ex2_launch(float lo, float hi, unsigned long long* out_max_rel_bits, cudaStream_t s);
+int test_bounds_launch(Ctl* ctl, long long index, long long n, cudaStream_t s);
+int build_checked();
 int test_l2_read_launch(const void* buf, size_t bytes, int iters, unsigned int* sink, int grid,
                         cudaStream_t s);
 int test_barrier_timeout_launch(Ctl* ctl, int grid, cudaStream_t s);

@@ -47,6 +47,19 @@ constexpr int MV_CLM = 23;             // footprint cells the agent must keep cl
 
 constexpr int kTail = 256;             // waiting movers one block finishes alone
 
+// Debug build: a mover entry names a replicate, a slot, a start cell inside
+// the grid and offsets within the path table (the movement-order pass only
+// writes such entries; this guards the rounds against anything else).
+__device__ __forceinline__ bool entry_ok(const StepArgs& a, const MoveEntry& e) {
+  if (!kChecked) return true;
+  const int rep = (int)(e.ref >> 24);
+  if (!fg_in(a.ctl, rep, a.n_rep)) return false;
+  const RepDev& R = a.reps[rep];
+  return fg_in(a.ctl, e.ref & 0xFFFFFFu, R.cap) && fg_in(a.ctl, e.c0 & 0xFFFFu, R.W) &&
+         fg_in(a.ctl, e.c0 >> 16, R.H) && fg_in(a.ctl, (long long)((e.info >> MV_DX) & 15u) - 3, 11) &&
+         fg_in(a.ctl, (long long)((e.info >> MV_DY) & 15u) - 3, 11);
+}
+
 // Claim value: an 8-bit round tag g (0..kTags-1; the value falls as g grows)
 // above the 24-bit priority, so a claim of a later round always wins
 // atomicMin over an older one.  Tags run on from step to step; the claim
@@ -157,9 +170,17 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
     }
     bool mover = false;
     MoveEntry e;
-    if (cell >= 0) {
-      ++alive_local;
-      const int des = R.desired[slot];
+    if (cell >= 0) ++alive_local;
+    // debug build: the agent's cell and desired cell inside the grid, the
+    // desired cell within the path table's reach (|dx|, |dy| <= 5)
+    const long long C = (long long)R.W * R.H;
+    const int des0 = cell >= 0 ? R.desired[slot] : -1;
+    const bool sane = !kChecked || cell < 0 ||
+                      (fg_in(a.ctl, cell, C) && fg_in(a.ctl, des0, C) &&
+                       fg_in(a.ctl, des0 % R.W - cell % R.W + 5, 11) &&
+                       fg_in(a.ctl, des0 / R.W - cell / R.W + 5, 11));
+    if (cell >= 0 && sane) {
+      const int des = des0;
       const int W = R.W;
       const int x0 = cell % W, y0 = cell / W;
       const int dx = des % W - x0, dy = des / W - y0;
@@ -516,6 +537,7 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
   // ---- claims of round 0, straight from the step's list
   for (uint32_t k = tid; k < nb; k += blockDim.x) {
     const MoveEntry e = a.act[2][mover_at(k)];
+    if (!entry_ok(a, e)) continue;
     const RepDev& R = a.reps[e.ref >> 24];
     int c[6], q[6];
     foot_cells(&tab, e.c0, R, e.info, c, q);
@@ -567,14 +589,16 @@ __global__ void __launch_bounds__(kMoveThreads, 2) k_move_rounds(StepArgs a) {
     }
   };
   for (uint32_t k = tid; k < nb; k += 2u * blockDim.x) {
-    const bool two = k + blockDim.x < nb;
+    bool two = k + blockDim.x < nb;
     const MoveEntry e1 = a.act[2][mover_at(k)];
     MoveEntry e2 = e1;
     if (two) e2 = a.act[2][mover_at(k + blockDim.x)];
+    const bool one = entry_ok(a, e1);
+    two = two && entry_ok(a, e2);
     uint32_t cl1[6], cl2[6];
-    r0_load(e1, cl1);
+    if (one) r0_load(e1, cl1);
     if (two) r0_load(e2, cl2);
-    r0_decide(e1, cl1);
+    if (one) r0_decide(e1, cl1);
     if (two) r0_decide(e2, cl2);
   }
   __syncthreads();

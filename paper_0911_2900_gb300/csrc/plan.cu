@@ -32,7 +32,7 @@ struct RcAgent {
   unsigned long long m0, m1;
   double S0, nks;
   const uint32_t* rec;
-  int cell, W, v, pad;
+  int cell, W, v, H;
 };
 
 __global__ void __launch_bounds__(kRcThreads) k_recheck(StepArgs a) {
@@ -61,17 +61,25 @@ __global__ void __launch_bounds__(kRcThreads) k_recheck(StepArgs a) {
   const int t = a.ctl->t;
   for (uint32_t q0 = blockIdx.x * kRcAgents; q0 < n; q0 += gridDim.x * kRcAgents) {
     // thread i < kRcAgents: agent q0 + i
-    const bool mine = tid < kRcAgents && q0 + tid < n;
+    bool mine = tid < kRcAgents && q0 + tid < n;
     int rep = 0, slot = 0, K = 0;
     uint32_t rec0 = 0;
     if (mine) {
       const uint32_t e = a.queue[q0 + tid];
       rep = (int)(e >> 24);
       slot = (int)(e & 0xFFFFFFu);
+      // debug build: the queue entry, the agent's cell and speed checked
+      if (kChecked)
+        mine = fg_in(a.ctl, rep, a.n_rep) && fg_in(a.ctl, slot, a.reps[rep].cap) &&
+               fg_in(a.ctl, a.reps[rep].cell[slot], (long long)a.reps[rep].W * a.reps[rep].H) &&
+               (!a.reps[rep].speed || fg_in(a.ctl, (long long)a.reps[rep].speed[slot] - 1, 5));
+    }
+    if (mine) {
       const RepDev& R = a.reps[rep];
       RcAgent x;
       x.cell = R.cell[slot];
       x.W = R.W;
+      x.H = R.H;
       x.v = R.speed ? (int)R.speed[slot] : R.v;  // the agent's own maximum speed
       x.rec = R.rec;
       rec0 = R.rec[x.cell];
@@ -81,7 +89,6 @@ __global__ void __launch_bounds__(kRcThreads) k_recheck(StepArgs a) {
       const int mw = s_K[x.v - 1] > 64 ? 2 : 1;
       x.m0 = mk[(size_t)x.cell * mw];
       x.m1 = (mw > 1) ? mk[(size_t)x.cell * mw + 1] : 0ull;
-      x.pad = 0;
       s_ag[tid] = x;
       K = s_K[x.v - 1];
     }
@@ -109,7 +116,9 @@ __global__ void __launch_bounds__(kRcThreads) k_recheck(StepArgs a) {
       if (mask_bit(x.m0, x.m1, k)) {
         const int dx = s_tab[x.v - 1][k][0], dy = s_tab[x.v - 1][k][1];
         const bool center = (dx == 0 && dy == 0);
-        const uint32_t r = x.rec[x.cell + dy * x.W + dx];
+        const bool in = !kChecked || fg_in(a.ctl, (long long)x.cell + dy * x.W + dx,
+                                            (long long)x.W * x.H);
+        const uint32_t r = in ? x.rec[x.cell + dy * x.W + dx] : REC_OCC;
         if (center || !(r & REC_OCC)) wk = exp64(__dmul_rn(x.nks, __dsub_rn(s64_of(r), x.S0)));
       }
       s_c[i][k] = wk;

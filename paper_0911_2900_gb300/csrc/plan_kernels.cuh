@@ -210,6 +210,8 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
       if (slot >= end) continue;
       const int cell = R.cell[slot];
       if (cell < 0 || other_speed<V>(R, slot)) continue;
+      const long long C = (long long)R.W * R.H;
+      if (!fg_in(a.ctl, cell, C)) continue;
       const int id = R.id[slot];
       const uint32_t rec0 = rec[cell];
       unsigned long long m0, m1;
@@ -220,7 +222,8 @@ __global__ void __launch_bounds__(256) k_plan_fp32(StepArgs a, Chunks ch, int no
 #pragma unroll
       for (int j = 0; j < Q; ++j) {
         const int k = sub * Q + j;
-        const bool adm = (k < K) && (k != CENTER) && mask_bit(m0, m1, k);
+        const bool adm = (k < K) && (k != CENTER) && mask_bit(m0, m1, k) &&
+                         (!kChecked || fg_in(a.ctl, (long long)cell + s_off[k], C));
         rr[j] = adm ? rec[cell + s_off[k]] : REC_OCC;
       }
       const float a0m = field_m(rec_a(rec0)), b0m = field_m(rec_b(rec0));
@@ -346,17 +349,22 @@ __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, 
   // grid) skips the per-candidate mask tests
   constexpr unsigned long long kFull0 = K >= 64 ? ~0ull : ((1ull << K) - 1ull);
   constexpr unsigned long long kFull1 = K > 64 ? ((1ull << (K - 64)) - 1ull) : 0ull;
+  // (debug build: every candidate's cell index checked against the grid)
+  const long long C = (long long)R.W * R.H;
   if (__all_sync(__activemask(), m0 == kFull0 && m1 == kFull1)) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int off = TILE ? (T.dy[k] * kTileP + T.dx[k]) : (T.dy[k] * pitch + T.dx[k]);
-      rr[k] = (k != CENTER) ? p0[off] : REC_OCC;
+      const bool adm = (k != CENTER) &&
+                       (!kChecked || fg_in(a.ctl, (long long)cell + T.dy[k] * R.W + T.dx[k], C));
+      rr[k] = adm ? p0[off] : REC_OCC;
     }
   } else {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int off = TILE ? (T.dy[k] * kTileP + T.dx[k]) : (T.dy[k] * pitch + T.dx[k]);
-      const bool adm = (k != CENTER) && mask_bit(m0, m1, k);
+      const bool adm = (k != CENTER) && mask_bit(m0, m1, k) &&
+                       (!kChecked || fg_in(a.ctl, (long long)cell + T.dy[k] * R.W + T.dx[k], C));
       rr[k] = adm ? p0[off] : REC_OCC;
     }
   }
@@ -393,6 +401,7 @@ __global__ void __launch_bounds__(256) k_plan_direct(StepArgs a, Chunks ch, int 
     if (slot >= end) continue;
     const int cell = R.cell[slot];
     if (cell < 0 || other_speed<V>(R, slot)) continue;
+    if (!fg_in(a.ctl, cell, (long long)R.W * R.H)) continue;
     plan_one_g1<V, REACH, DIAG, false>(a, R, rep, slot, cell, R.rec + cell, R.W, t, norecheck,
                                        s_dxdy);
   }
@@ -412,7 +421,8 @@ __global__ void __launch_bounds__(256, 2) k_plan_tile(StepArgs a, Chunks ch, int
     const RepDev& R = a.reps[rep];
     const int end = min(ch.begin[c] + kChunk, a.n_slots[rep]);
     const int slot = ch.begin[c] + threadIdx.x;
-    const int cell = (slot < end && !other_speed<V>(R, slot)) ? R.cell[slot] : -1;
+    int cell = (slot < end && !other_speed<V>(R, slot)) ? R.cell[slot] : -1;
+    if (cell >= 0 && !fg_in(a.ctl, cell, (long long)R.W * R.H)) cell = -1;
     const bool live = cell >= 0;
     const int W = R.W;
     int x = 0, y = 0;
@@ -531,6 +541,7 @@ __global__ void __launch_bounds__(128) k_plan_fp64(StepArgs a, Chunks ch) {
     for (int slot = begin + threadIdx.x; slot < end; slot += blockDim.x) {
       const int cell = R.cell[slot];
       if (cell < 0 || other_speed<V>(R, slot)) continue;
+      if (!fg_in(a.ctl, cell, (long long)R.W * R.H)) continue;
       const uint32_t rec0 = R.rec[cell];
       const int target = plan_fp64_one<V, REACH>(R, s_off, cell, R.id[slot], t, nullptr);
       R.desired[slot] = target;
@@ -562,6 +573,7 @@ __global__ void __launch_bounds__(128) k_diag_compare(StepArgs a, Chunks ch) {
     for (int slot = begin + threadIdx.x; slot < end; slot += blockDim.x) {
       const int cell = R.cell[slot];
       if (cell < 0 || other_speed<V>(R, slot)) continue;
+      if (!fg_in(a.ctl, cell, (long long)R.W * R.H)) continue;
       double cum[K];
       const int target = plan_fp64_one<V, REACH>(R, s_off, cell, R.id[slot], t, cum);
       const int64_t di = a.diag_base[rep] + slot;

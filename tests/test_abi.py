@@ -105,3 +105,17 @@ def test_plan_noalloc_checks_the_output_tensor():
         ctx.plan_noalloc(0, 0, torch.zeros(8, dtype=torch.int32))
     with pytest.raises(ValueError, match="must be on"):
         ctx.plan_noalloc(0, 0, torch.zeros(8, dtype=torch.int32, device="meta"))
+
+
+def test_checked_build_exports_the_same_boundary():
+    """The debug build (index checks in the kernels) is a drop-in for the
+    release library: the same declared symbols, and each reports which build
+    it is (a host-only call)."""
+    from paper_0911_2900_gb300 import build
+
+    rel = C.CDLL(build.build())
+    chk = C.CDLL(build.build(checked=True))
+    missing = [n for n in declared_functions() if not hasattr(chk, n)]
+    assert not missing, missing
+    rel.fast_build_checked.restype = chk.fast_build_checked.restype = C.c_int
+    assert rel.fast_build_checked() == 0 and chk.fast_build_checked() == 1
