@@ -514,3 +514,67 @@ def test_stress_form_from_start(fg, orc):
     o = run_oracle(orc, w, steps, threads=os.cpu_count() or 1)
     assert_same(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd), o, steps)
     assert st["alive"] + st["exited"] == len(w.cells)
+
+
+# --------------------------------------------------------------------------- speeds per agent
+def _speeds(n, seed, lo=1, hi=5):
+    return np.random.default_rng(seed).integers(lo, hi + 1, n).astype(np.uint8)
+
+
+@pytest.mark.parametrize("precision,lanes", [("fp64", None), ("fp32_recheck", 0),
+                                             ("fp32_recheck", 1), ("fp32_recheck", 2),
+                                             ("fp32_recheck", 4), ("fp32_recheck", 8)])
+def test_per_agent_speeds(fg, orc, precision, lanes):
+    """Agents of one replicate with maximum speeds 1..5 of their own: each
+    speed's planning launch plans only its agents, over its reach set and
+    line-of-sight mask; the re-sort keeps the speed classes apart; the FP64
+    re-check uses each agent's speed.  Bit-equal to the oracle."""
+    w = wl.config_small_room(W=80, H=60, n=1500, seed=21, v_m=3)
+    sp = _speeds(len(w.cells), 5)
+    lanes_by_v = None if lanes is None else {v: lanes for v in range(1, 6)}
+    steps = 60
+    _, (g,) = run_gpu(fg, [w], steps, precision, speeds=[sp], lanes=lanes_by_v)
+    o = run_oracle(orc, w, steps, speeds=sp)
+    assert_same(g, o, steps)
+
+
+def test_per_agent_speeds_batched_with_uniform_replicates(fg, orc):
+    """A batch mixing replicates with speeds per agent and replicates with one
+    speed: every replicate joins the planning launch of each speed it has."""
+    ws = [wl.config_small_room(W=50 + 10 * i, H=40, n=500 + 100 * i, seed=30 + i, v_m=1 + i)
+          for i in range(4)]
+    sps = [_speeds(len(ws[0].cells), 7, 2, 4), None, _speeds(len(ws[2].cells), 8), None]
+    steps = 40
+    _, gs = run_gpu(fg, ws, steps, "fp32_recheck", speeds=sps)
+    for w, sp, g in zip(ws, sps, gs):
+        assert_same(g, run_oracle(orc, w, steps, speeds=sp), steps)
+
+
+def test_speeds_equal_to_v_m_change_nothing(fg, orc):
+    w = wl.config_small_room(W=60, H=50, n=800, seed=41, v_m=4)
+    steps = 30
+    _, (a,) = run_gpu(fg, [w], steps)
+    _, (b,) = run_gpu(fg, [w], steps, speeds=[np.full(len(w.cells), 4, np.uint8)])
+    assert np.array_equal(a["dig_cell"], b["dig_cell"])
+    assert np.array_equal(a["dig_des"], b["dig_des"])
+    assert np.array_equal(a["cells"], b["cells"])
+
+
+def test_speeds_are_checked_by_the_library(fg):
+    w = wl.config_small_room(W=30, H=30, n=50, seed=2, v_m=2)
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    with pytest.raises(fg.FastError):
+        ctx.set_speeds(0, np.array([1, 0, 3], np.uint8))  # speed 0
+    with pytest.raises(fg.FastError):
+        ctx.set_speeds(0, np.array([6], np.uint8))  # speed 6
+    ctx.set_speeds(0, np.full(10, 3, np.uint8))  # fewer ids than agents
+    with pytest.raises(fg.FastError):
+        ctx.place(0, w.cells)
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)  # drops the speeds
+    ctx.set_speeds(0, np.full(len(w.cells), 3, np.uint8))
+    ctx.place(0, w.cells)
+    with pytest.raises(fg.FastError):
+        ctx.set_speeds(0, np.full(len(w.cells), 2, np.uint8))  # agents already placed
+    ctx.step(3)
+    ctx.close()

@@ -106,3 +106,23 @@ def test_plan_noalloc_rejects_more_slots_than_its_scratch(fg):
     torch.cuda.synchronize()
     assert int((out != -7).sum()) == 0
     ctx.close()
+
+
+def test_plan_noalloc_refuses_speeds_per_agent(fg):
+    """A replicate whose agents have speeds of their own is refused with
+    FAST_EINVAL before anything is queued; the output stays untouched."""
+    import torch
+
+    w = wl.config_small_room(W=40, H=30, n=200, seed=3, v_m=3)
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx.set_speeds(0, np.full(len(w.cells), 2, np.uint8))
+    ctx.place(0, w.cells)
+    ctx.plan_only(1)
+    out = torch.full((len(w.cells),), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(fg.FastError) as e:
+        ctx.plan_noalloc(0, 0, out)
+    assert e.value.code == -1
+    torch.cuda.synchronize()
+    assert int((out != -7).sum()) == 0
+    ctx.close()
