@@ -141,7 +141,7 @@ __device__ __forceinline__ int path_offset(int num, float invL) {
   return num < 0 ? -r : r;
 }
 
-__global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
+__global__ void __launch_bounds__(256, 8) k_move_prep(StepArgs a, Chunks ch) {
   // a new claim epoch starts with clean claim and mark arrays (the rounds
   // kernel then starts its tags and stamps from the beginning)
   if (epoch_ends(a.ctl)) clear_all_claims(a, false, true);
@@ -152,12 +152,21 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
   unsigned alive_local = 0, foot_local = 0;
   int krep = -1;
   U4 k;
+  int nrep = blockIdx.x < ch.n ? ch.rep[blockIdx.x] : 0;
+  int nbeg = blockIdx.x < ch.n ? ch.begin[blockIdx.x] : 0;
   for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {  // the same chunks for the whole block
-    const int rep = ch.rep[c];
+    const int rep = nrep;
     const RepDev& R = a.reps[rep];
-    const int end = min(ch.begin[c] + kChunk, a.n_slots[rep]);
-    const int slot = ch.begin[c] + threadIdx.x;
+    const int end = min(nbeg + kChunk, a.n_slots[rep]);
+    const int slot = nbeg + threadIdx.x;
+    // the agent's cell, desired cell and id together; the next chunk's place
     const int cell = slot < end ? R.cell[slot] : -1;
+    const int des_ld = slot < end ? R.desired[slot] : -1;
+    const uint32_t id_ld = slot < end ? (uint32_t)R.id[slot] : 0u;
+    if (c + (int)gridDim.x < ch.n) {
+      nrep = ch.rep[c + gridDim.x];
+      nbeg = ch.begin[c + gridDim.x];
+    }
     // the replicate's movement-order keys for this step (one Philox block
     // per warp, shared; kept while the block's chunks stay in one replicate)
     if (rep != krep) {
@@ -174,7 +183,7 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
     // debug build: the agent's cell and desired cell inside the grid, the
     // desired cell within the path table's reach (|dx|, |dy| <= 5)
     const long long C = (long long)R.W * R.H;
-    const int des0 = cell >= 0 ? R.desired[slot] : -1;
+    const int des0 = cell >= 0 ? des_ld : -1;
     const bool sane = !kChecked || cell < 0 ||
                       (fg_in(a.ctl, cell, C) && fg_in(a.ctl, des0, C) &&
                        fg_in(a.ctl, des0 % R.W - cell % R.W + 5, 11) &&
@@ -225,7 +234,7 @@ __global__ void __launch_bounds__(256) k_move_prep(StepArgs a, Chunks ch) {
         foot_local += (unsigned)fp + 1u;
         e.c0 = ((uint32_t)y0 << 16) | (uint32_t)x0;
         e.ref = ((uint32_t)rep << 24) | (uint32_t)slot;
-        e.prio = move_priority((uint32_t)R.id[slot], k);
+        e.prio = move_priority(id_ld, k);
         e.info = (uint32_t)fp | ex | ((uint32_t)(dx + 8) << MV_DX) |
                  ((uint32_t)(dy + 8) << MV_DY) | ((uint32_t)fin << MV_FIN) |
                  (gone ? MV_GONE : 0u);

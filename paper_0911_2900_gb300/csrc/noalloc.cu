@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(128) k_noalloc_plan(RepDev R, int32_t cap, int
     const unsigned long long m0 = R.mask[(size_t)cell * R.mw];
     const unsigned long long m1 = (K > 64) ? R.mask[(size_t)cell * R.mw + 1] : 0ull;
     const int a0 = rec_a(rec0), b0 = rec_b(rec0);
-    float w[K];
+    float cw[K];  // cumulative weights C_k
     float Wt = 0.f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -67,12 +67,12 @@ __global__ void __launch_bounds__(128) k_noalloc_plan(RepDev R, int32_t cap, int
         const uint32_t r = R.rec[cell + s_off[k]];
         if (!(r & REC_OCC)) wk = ex2_approx(ds32(rec_a(r) - a0, rec_b(r) - b0) * R.c32);
       }
-      w[k] = wk;
       Wt += wk;
+      cw[k] = Wt;
     }
     const float u = plan_uniform24((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
     bool certain = false;
-    const int found = fp32_pick<K>(Wt, u, R.margin, [&](int k) { return w[k]; }, certain);
+    const int found = fp32_pick<K>(Wt, u, R.margin, [&](int k) { return cw[k]; }, certain);
     if (certain) {
       if (id < bound) out[id] = cell + s_off[found];
     } else {

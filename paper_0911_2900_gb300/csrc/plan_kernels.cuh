@@ -109,47 +109,45 @@ __device__ __forceinline__ float rec_weight(uint32_t r, float a0m, float b0m, fl
 }
 
 // The FP32 draw of one agent: r = u*W against the cumulative weights
-// C_k = w(0) + ... + w(k) in canonical order; the choice is the first k with
-// r < C_k (a zero weight leaves C unchanged and so is never first; no such k
-// only through rounding, which the FP64 rule then settles).  Returns k (-1:
-// none) and sets `certain` when r lies farther than margin*W from both
-// boundaries C_{k-1} and C_k of that k: only then is the FP32 choice sure to
-// be the FP64 rule's (the margin bounds the FP32 weights' and sums' error).
-template <int K, typename WF>
-__device__ __forceinline__ int fp32_pick(float Wt, float u, float margin, WF w, bool& certain) {
+// C_k = w(0) + ... + w(k), summed in canonical order (C(k) returns them; W is
+// the last).  The choice is the first k with r < C_k.  C never decreases (a
+// zero weight leaves it unchanged and so is never first), so that k is the
+// number of C_k <= r; K of them means none, only through rounding, which the
+// FP64 rule then settles.  Returns k (-1: none) and sets `certain` when r
+// lies farther than margin*W from both boundaries C_{k-1} (0 for k = 0) and
+// C_k of that k: only then is the FP32 choice sure to be the FP64 rule's (the
+// margin bounds the FP32 weights' and sums' error).
+template <int K, typename CF>
+__device__ __forceinline__ int fp32_pick(float Wt, float u, float margin, CF C, bool& certain) {
   const float r = __fmul_rn(u, Wt);
-  float cacc = 0.f, cprev = 0.f, ck = 0.f;
-  int found = -1;
+  int below = 0;
+  float lo = 0.f, hi = __int_as_float(0x7F800000);  // the boundaries around r
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    const float cn = cacc + w(k);
-    const bool hit = (found < 0) && (r < cn);
-    found = hit ? k : found;
-    cprev = hit ? cacc : cprev;
-    ck = hit ? cn : ck;
-    cacc = cn;
+    const float ck = C(k);
+    const bool le = ck <= r;
+    below += le ? 1 : 0;
+    lo = le ? ck : lo;
+    hi = le ? hi : fminf(hi, ck);
   }
+  const int found = below < K ? below : -1;
   const float mw = margin * Wt;
-  certain = (found >= 0) && (r > cprev + mw) && (r < ck - mw);
+  certain = (found >= 0) && (r > lo + mw) && (r < hi - mw);
   return found;
 }
 
 // Shared end of the one-thread kernels: the draw and margin test
 // (fp32_pick), and the outputs.
-template <int K, int CENTER, bool DIAG, typename WF>
+template <int K, int CENTER, bool DIAG, typename CF>
 __device__ __forceinline__ void finish_g1(const StepArgs& a, const RepDev& R, int rep, int slot,
                                           int cell, float Wt, float u, float margin,
-                                          int norecheck, const int* s_dxdy, WF w) {
+                                          int norecheck, const int* s_dxdy, CF C) {
   bool ok = false;
-  const int found = fp32_pick<K>(Wt, u, margin, w, ok);
+  const int found = fp32_pick<K>(Wt, u, margin, C, ok);
   if (DIAG) {
     float* dp = a.diag_p32 + (a.diag_base[rep] + slot) * (int64_t)kMaxK;
-    float cc = 0.f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      cc = cc + w(k);
-      dp[k] = cc / Wt;
-    }
+    for (int k = 0; k < K; ++k) dp[k] = C(k) / Wt;
   }
   const int dd = s_dxdy[found >= 0 ? found : CENTER];
   const int target = cell + ((dd >> 8) - 16) * R.W + ((dd & 0xFF) - 16);
@@ -370,17 +368,17 @@ __device__ __forceinline__ void plan_one_g1(const StepArgs& a, const RepDev& R, 
   }
   const float a0m = field_m(rec_a(rec0)), b0m = field_m(rec_b(rec0));
   const float c32 = R.c32;
-  float w[K];
+  float cw[K];  // cumulative weights C_k
   float Wt = 0.f;
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     const float wk = (k == CENTER) ? 1.0f : rec_weight(rr[k], a0m, b0m, c32);
-    w[k] = wk;
     Wt += wk;
+    cw[k] = Wt;
   }
   const float u = plan_uniform24((uint32_t)id, (uint32_t)t, R.seed_lo, R.seed_hi);
   finish_g1<K, CENTER, DIAG>(a, R, rep, slot, cell, Wt, u, R.margin_v[V - 1], norecheck, s_dxdy,
-                             [&](int k) { return w[k]; });
+                             [&](int k) { return cw[k]; });
 }
 
 // ---------------------------------------------------------------------------
