@@ -192,14 +192,35 @@ __global__ void k_bucket_zero(StepArgs a) {
     a.bucket_count[i] = 0u;
 }
 
+// The agents of a warp are mostly in one or two buckets (they were sorted by
+// bucket the last time): lanes with the same bucket make one atomic together.
+// Returns, for lane `lane`, its bucket (-1: none), the lanes that share it and
+// whether it leads them (the lowest of them).
+struct BucketGroup {
+  int bucket;
+  unsigned lanes;
+  bool leader;
+};
+
+__device__ __forceinline__ BucketGroup bucket_group(const RepDev& R, int cell, int slot, bool valid) {
+  const int lane = threadIdx.x & 31;
+  BucketGroup g;
+  g.bucket = valid ? bucket_of(R, cell, slot) : -1;
+  // lanes without an agent get keys of their own
+  g.lanes = __match_any_sync(0xffffffffu, valid ? g.bucket : -1 - lane);
+  g.leader = valid && (__ffs(g.lanes) - 1 == lane);
+  return g;
+}
+
 __global__ void k_bucket_count(StepArgs a, Chunks ch) {
-  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {  // the same chunks for the whole block
     const int rep = ch.rep[c];
     const RepDev& R = a.reps[rep];
     const int slot = ch.begin[c] + threadIdx.x;
-    if (slot >= min(ch.begin[c] + kChunk, a.n_slots[rep])) continue;
-    const int cell = R.cell[slot];
-    if (cell >= 0) atomicAdd(&a.bucket_count[bucket_of(R, cell, slot)], 1u);
+    const bool in = slot < min(ch.begin[c] + kChunk, a.n_slots[rep]);
+    const int cell = in ? R.cell[slot] : -1;
+    const BucketGroup g = bucket_group(R, cell, slot, cell >= 0);
+    if (g.leader) atomicAdd(&a.bucket_count[g.bucket], (uint32_t)__popc(g.lanes));
   }
 }
 
@@ -293,14 +314,21 @@ __global__ void k_bucket_scan_reps(StepArgs a) {
 }
 
 __global__ void k_bucket_scatter(StepArgs a, Chunks ch) {
-  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+  const unsigned below = (1u << (threadIdx.x & 31)) - 1u;
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {  // the same chunks for the whole block
     const int rep = ch.rep[c];
     const RepDev& R = a.reps[rep];
     const int slot = ch.begin[c] + threadIdx.x;
-    if (slot >= min(ch.begin[c] + kChunk, a.n_slots[rep])) continue;
-    const int cell = R.cell[slot];
+    const bool in = slot < min(ch.begin[c] + kChunk, a.n_slots[rep]);
+    const int cell = in ? R.cell[slot] : -1;
+    const BucketGroup g = bucket_group(R, cell, slot, cell >= 0);
+    // the group's leader takes its places in the bucket, every lane its own
+    // one in lane order
+    uint32_t base = 0u;
+    if (g.leader) base = atomicAdd(&a.bucket_count[g.bucket], (uint32_t)__popc(g.lanes));
+    base = __shfl_sync(0xffffffffu, base, g.bucket >= 0 ? __ffs(g.lanes) - 1 : 0);
     if (cell < 0) continue;
-    const uint32_t pos = atomicAdd(&a.bucket_count[bucket_of(R, cell, slot)], 1u) -
+    const uint32_t pos = base + (uint32_t)__popc(g.lanes & below) -
                          a.bucket_count[a.n_buckets + 1 + 2 * rep];
     R.id2[pos] = R.id[slot];
     R.cell2[pos] = cell;

@@ -17,8 +17,11 @@ int diag_launch_v4(const StepArgs&, int, const Chunks&, int, cudaStream_t);
 int diag_launch_v5(const StepArgs&, int, const Chunks&, int, cudaStream_t);
 
 // ---------------------------------------------------------------------------
-// FP64 re-check of the queued agents, kRcAgents agents per block of 256
-// threads.  The threads share out all FP64 weights of the block's agents (the
+// FP64 re-check of the queued agents, A agents per block of 256 threads:
+// A = kRcAgents (8) when the queue is long, fewer when it is short, so that
+// the few agents of a short queue spread over more SMs (the queue's length is
+// known on the device only; the grid is sized for a long one).  The threads
+// share out all FP64 weights of the block's agents (the
 // flattened list of (agent, candidate) pairs, about one exp64 per thread, so
 // their long FP64 latencies overlap and every FP64 instruction is full), then
 // thread i forms agent i's cumulative sums C_k sequentially in canonical
@@ -42,7 +45,8 @@ __global__ void __launch_bounds__(kRcThreads) k_recheck(StepArgs a) {
   __shared__ RcAgent s_ag[kRcAgents];
   __shared__ double s_c[kRcAgents][kMaxK];  // weights, then C_k
   const uint32_t n = min(a.ctl->q_count, a.q_cap);
-  if ((uint32_t)blockIdx.x * kRcAgents >= n) return;
+  const uint32_t A = n <= gridDim.x / 8u ? 2u : (n <= gridDim.x / 2u ? 4u : (uint32_t)kRcAgents);
+  if ((uint32_t)blockIdx.x * A >= n) return;
   const int reach = a.reps[0].reach;  // one reach set per context
   if (threadIdx.x < 5) {
     const int v = threadIdx.x + 1;
@@ -59,9 +63,10 @@ __global__ void __launch_bounds__(kRcThreads) k_recheck(StepArgs a) {
   __syncthreads();
   const int tid = threadIdx.x;
   const int t = a.ctl->t;
-  for (uint32_t q0 = blockIdx.x * kRcAgents; q0 < n; q0 += gridDim.x * kRcAgents) {
-    // thread i < kRcAgents: agent q0 + i
-    bool mine = tid < kRcAgents && q0 + tid < n;
+  for (uint32_t q0 = blockIdx.x * A; q0 < n; q0 += gridDim.x * A) {
+    // thread i < A: agent q0 + i (threads A..kRcAgents-1 have no agent and
+    // no candidates)
+    bool mine = (uint32_t)tid < A && q0 + tid < n;
     int rep = 0, slot = 0, K = 0;
     uint32_t rec0 = 0;
     if (mine) {

@@ -492,6 +492,24 @@ def test_precision_form_full_length(fg, orc):
     assert_same(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd), o, steps)
 
 
+def test_recheck_mid_length_queue(fg, orc):
+    """The FP64 re-check takes 2, 4 or 8 queued agents per block by the
+    queue's length (2 up to one agent per 8 blocks of its 16-per-SM grid, 4 up
+    to one per 2 blocks); the corridors and precision workloads take 2 and 8.
+    A quarter-size clustered workload (2000x2000, 250k agents) queues a
+    length in between: its 12 steps from the start equal the oracle's."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    w = wl.config_precision(side=2000, n=250_000)
+    steps = 12
+    ctx, (g,) = run_gpu(fg, [w], steps, "fp32_recheck")
+    per_step = g["stats"]["rechecked"] / steps
+    assert 2 * sms < per_step <= 8 * sms, per_step
+    assert_same(g, run_oracle(orc, w, steps, threads=os.cpu_count() or 1), steps)
+    ctx.close()
+
+
 def test_stress_form_from_start(fg, orc):
     """16384x16384, 10M uniform agents, v_m=5, FP32 + FP64 re-check, spatial
     re-sort every 8 steps: 24 steps from the workload's own start (three
