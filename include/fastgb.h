@@ -201,7 +201,12 @@ int fast_set_speeds(fast_ctx* ctx, int32_t replicate, int32_t n_ids, const uint8
  * that fast_readback writes can be placed again as it is);
  * start_step: index of the next step (all replicates share one step index;
  * resuming a run = placing its read-back state with its step index).
- * The cells and ids are checked on the device.  Errors: FAST_EINVAL (a cell
+ * The cells and ids are checked on the device.  Placing implicit ids again
+ * with the same n keeps every agent in the storage slot its id holds (ids
+ * without one are added after the others), so the spatial order of the
+ * agents in memory stays and the next step does not sort them first; any
+ * other placement stores agent i in slot i and sorts before the next step.
+ * The storage order never changes a result.  Errors: FAST_EINVAL (a cell
  * outside the grid, on a wall, unreachable, an exit or taken twice, an id
  * out of range or repeated, or an id without a speed after fast_set_speeds;
  * the replicate is then left without agents),
@@ -226,10 +231,12 @@ int fast_step(fast_ctx* ctx, int32_t n_steps);
  * used to time the planning phase alone. */
 int fast_plan_only(fast_ctx* ctx, int32_t n);
 
-/* Waits for the stream, then writes, for ids 0..id_bound-1, the cell of each
- * agent of the replicate (-1: left or not present) and its desired cell of
- * the last planning pass (-1 likewise); either pointer may be NULL.  stats may
- * be NULL.  Errors: FAST_EINVAL, FAST_ETIMEOUT / FAST_ECUDA (device error). */
+/* Queues, after the work on the stream, the copies of the cell of each agent
+ * of the replicate for ids 0..id_bound-1 (-1: left or not present) and of its
+ * desired cell of the last planning pass (-1 likewise), then waits for them;
+ * either pointer may be NULL.  stats may be NULL.  Errors: FAST_EINVAL,
+ * FAST_ETIMEOUT / FAST_ECUDA (device error; the arrays' contents are then
+ * unspecified). */
 int fast_readback(fast_ctx* ctx, int32_t replicate, int32_t id_bound, int32_t* cells_by_id,
                   int32_t* desired_by_id, fast_stats* stats);
 

@@ -47,11 +47,16 @@ struct RepHost {
   uint64_t seed = 0;
   int32_t cap = 0;                 // agent slots allocated
   int32_t n = 0;                   // agents placed
+  int32_t n_ids = -1;              // ids of the last placement if they were implicit (0..n-1)
   uint32_t speed_set = 0;          // speeds given per agent (bit s-1: speed s), 0: all v
   uint8_t* d_speed_by_id = nullptr;  // device copy of the speeds by id
   int32_t n_speed_ids = 0;
   RepDev d{};                      // device pointers and parameters
 };
+
+// Pinned staging of the batched calls: BatchRep per replicate, then error
+// words (3), slot counts and exit counts per replicate, then 16 spare words.
+constexpr size_t kBatchHostBytes = sizeof(BatchRep) * kMaxRep + 4 * 5 * kMaxRep + 64;
 
 // Speeds whose planning launch covers this replicate.
 uint32_t speeds_of(const RepHost& R) { return R.speed_set ? R.speed_set : 1u << (R.v - 1); }
@@ -80,6 +85,8 @@ struct fast_ctx {
   uint32_t* d_queue = nullptr;
   MoveEntry* d_act[3] = {nullptr, nullptr, nullptr};
   uint32_t* d_mv_prio = nullptr;
+  Ctl* h_ctl = nullptr;      // pinned: a copy of the control block, then 16 words (an exit
+                             // count read back with the data; placement's small copies)
   uint32_t* d_mv[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 
   uint32_t list_cap = 0;
@@ -95,8 +102,6 @@ struct fast_ctx {
   int32_t* d_place_err = nullptr;  // placement check: first bad index, agents placed
   int32_t* d_stage = nullptr;      // fast_place_all: the uploaded cells of all replicates
   int64_t stage_cap = 0;
-  int32_t* d_place_errs = nullptr;  // fast_place_all: per replicate as d_place_err
-  int32_t err_cap = 0;
 
   struct Group {
     int v = 0;
@@ -120,6 +125,11 @@ struct fast_ctx {
   };
   std::map<std::pair<int, int>, Multi> multi;
   cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t ev_upload = nullptr;  // placement: the cells' upload on the private stream is done
+  BatchRep* d_bp = nullptr;        // batched placement / read-back: per replicate
+  int32_t* d_berr = nullptr;       // its per-replicate error words (3 each)
+  char* h_batch = nullptr;         // pinned: BatchRep[kMaxRep], then 3+1+1 words per
+                                   // replicate (errors, slots, exits), then 16 words
   bool ran_step = false;
   int64_t launches = 0;          // kernels queued by this context
   int launches_per_graph[2] = {0, 0};
@@ -559,10 +569,8 @@ int write_ctl_int(fast_ctx* c, size_t offset, int32_t v) {
   return FAST_OK;
 }
 
-int check_device_error(fast_ctx* c) {
-  Ctl h{};
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  CUDA_TRY(c, cudaMemcpy(&h, c->d_ctl, sizeof h, cudaMemcpyDeviceToHost));
+// The error a copy of the control block records, as the call's result.
+int device_error_of(fast_ctx* c, const Ctl& h) {
   if (h.err == kDevErrTimeout)
     return fail(c, FAST_ETIMEOUT, "a device-side wait exceeded its limit (%lld ns)",
                 (long long)c->barrier_ns);
@@ -573,6 +581,35 @@ int check_device_error(fast_ctx* c) {
   return FAST_OK;
 }
 
+int check_device_error(fast_ctx* c) {
+  Ctl h{};
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  CUDA_TRY(c, cudaMemcpy(&h, c->d_ctl, sizeof h, cudaMemcpyDeviceToHost));
+  return device_error_of(c, h);
+}
+
+}  // namespace
+
+namespace {
+// Views of the pinned staging of the batched calls.
+struct BatchHost {  // views of the pinned staging of the batched calls
+  BatchRep* bp;
+  int32_t *err, *slots, *exited, *misc;
+};
+BatchHost batch_host(fast_ctx* c) {
+  BatchHost h;
+  h.bp = reinterpret_cast<BatchRep*>(c->h_batch);
+  h.err = reinterpret_cast<int32_t*>(c->h_batch + sizeof(BatchRep) * kMaxRep);
+  h.slots = h.err + 3 * kMaxRep;
+  h.exited = h.slots + kMaxRep;
+  h.misc = h.exited + kMaxRep;
+  return h;
+}
+int batch_buffers(fast_ctx* c) {
+  if (c->d_bp) return FAST_OK;
+  if (int e = alloc_into(c, &c->d_bp, kMaxRep)) return e;
+  return alloc_into(c, &c->d_berr, 3 * kMaxRep);
+}
 }  // namespace
 
 // ===========================================================================
@@ -636,6 +673,9 @@ static int create_impl(fast_ctx* c, int32_t n_replicates) {
   if (int e = alloc_into(c, &c->d_exited, n_replicates)) return e;
   for (auto& ev : c->ev) CUDA_TRY(c, cudaEventCreate(&ev));
   CUDA_TRY(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+  CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_ctl), sizeof(Ctl) + 64));
+  CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_upload, cudaEventDisableTiming));
+  CUDA_TRY(c, cudaMallocHost(reinterpret_cast<void**>(&c->h_batch), kBatchHostBytes));
   c->cur = c->stream;
   Ctl h{};
   h.resort_period = c->resort_period;
@@ -745,6 +785,7 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   CUDA_TRY(c, cudaMemsetAsync(d.cmark, 0, claim_cells, c->stream));
   R.grid_set = true;
   R.placed = false;
+  R.n_ids = -1;
   R.n = 0;
   const int32_t zero = 0;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots + r, &zero, 4, cudaMemcpyHostToDevice, c->stream));
@@ -821,72 +862,102 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
   const int64_t C = (int64_t)R.W * R.H;
 
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // The same implicit ids again (a caller that places what it read back):
+  // every agent goes back to the slot its id holds, so the storage order the
+  // last spatial sort made stays, and no sort is needed before the next step
+  // (agents move at most a few cells per step).
+  const bool keep_order = R.placed && !ids && n > 0 && n == R.n_ids && n <= R.cap;
+  int32_t* slot_of_id = keep_order ? R.d.id2 : nullptr;  // free scratch of cap slots here
+  if (keep_order) CUDA_TRY(c, cudaMemsetAsync(slot_of_id, 0xFF, (size_t)n * 4, c->stream));
   // clear the previous agents' occupancy marks
-  if (R.placed && R.cap > 0) LAUNCH_TRY(c, clear_occ_launch(c->d_reps + r, c->d_nslots, r, R.cap, c->stream));
+  if (R.placed && R.cap > 0)
+    LAUNCH_TRY(c, clear_occ_launch(c->d_reps + r, c->d_nslots, r, R.cap, slot_of_id, n, c->stream));
   if (n > R.cap || !R.placed)
     if (int e = realloc_slots(c, R, n)) return e;
+  // the upload runs on the private stream beside the clean-up below (the
+  // staging arrays are free: the stream was idle when this call began)
+  if (n > 0) {
+    CUDA_TRY(c, cudaMemcpyAsync(R.d.cell2, cells, (size_t)n * 4, cudaMemcpyHostToDevice,
+                                c->cap_stream));
+    if (ids)
+      CUDA_TRY(c, cudaMemcpyAsync(R.d.id2, ids, (size_t)n * 4, cudaMemcpyHostToDevice,
+                                  c->cap_stream));
+  }
+  CUDA_TRY(c, cudaEventRecord(c->ev_upload, c->cap_stream));
   if (ids && !c->d_id_bits) {
     if (int e = alloc_into(c, &c->d_id_bits, (size_t)1 << (kMaxIdBits - 5))) return e;
     CUDA_TRY(c, cudaMemsetAsync(c->d_id_bits, 0, (size_t)4 << (kMaxIdBits - 5), c->stream));
   }
   if (!c->d_place_err)
-    if (int e = alloc_into(c, &c->d_place_err, 2)) return e;
+    if (int e = alloc_into(c, &c->d_place_err, 4)) return e;
   R.placed = true;
   R.n = 0;
+  R.n_ids = -1;
   CUDA_TRY(c, cudaMemsetAsync(R.d.cell, 0xFF, (size_t)R.cap * 4, c->stream));
-  const int32_t init[2] = {INT32_MAX, 0};
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_place_err, init, 8, cudaMemcpyHostToDevice, c->stream));
-  if (n > 0) {
-    CUDA_TRY(c, cudaMemcpyAsync(R.d.cell2, cells, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
-    if (ids)
-      CUDA_TRY(c, cudaMemcpyAsync(R.d.id2, ids, (size_t)n * 4, cudaMemcpyHostToDevice, c->stream));
-  }
+  // first failing index, agents placed, slots appended, and the slot count
+  // before this call
+  int32_t* words = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(c->h_ctl) + sizeof(Ctl));
+  words[0] = INT32_MAX;
+  words[1] = 0;
+  words[2] = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_place_err, words, 12, cudaMemcpyHostToDevice, c->stream));
   if (c->layout_dirty) {
     if (int e = rebuild_layout(c)) return e;
   }
-  // the check and the placement in one pass on the device (slots 0..n-1)
+  CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->ev_upload, 0));
+  // the check and the placement in one pass on the device
   uint8_t* placed = reinterpret_cast<uint8_t*>(R.d.mvinfo);
   LAUNCH_TRY(c, place_checked_launch(c->d_reps + r, R.d.cell2, ids ? R.d.id2 : nullptr, n, C,
                                      c->d_id_bits, placed, R.d_speed_by_id, R.n_speed_ids,
-                                     c->d_place_err, c->stream));
-  int32_t res[2] = {INT32_MAX, 0};
-  CUDA_TRY(c, cudaMemcpyAsync(res, c->d_place_err, 8, cudaMemcpyDeviceToHost, c->stream));
+                                     slot_of_id, c->d_nslots + r, c->d_place_err, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(words + 4, c->d_place_err, 12, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(words + 7, c->d_nslots + r, 4, cudaMemcpyDeviceToHost, c->stream));
   if (ids)
     CUDA_TRY(c, cudaMemsetAsync(c->d_id_bits, 0, (size_t)4 << (kMaxIdBits - 5), c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const int32_t res0 = words[4], res1 = words[5], appended = words[6], slots_old = words[7];
   const int32_t zero = 0;
-  if (res[0] != INT32_MAX) {
-    // undo: the replicate is left without agents
+  if (res0 != INT32_MAX) {
+    // undo: the replicate is left without agents (every slot this call wrote
+    // is below n)
     LAUNCH_TRY(c, place_rollback_launch(c->d_reps + r, R.d.cell2, n, placed, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots + r, &zero, 4, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->d_exited + r, &zero, 4, cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    int32_t bad_cell = -1, bad_id = res[0];
-    if (cells) bad_cell = cells[res[0]];
-    if (ids) bad_id = ids[res[0]];
+    int32_t bad_cell = -1, bad_id = res0;
+    if (cells) bad_cell = cells[res0];
+    if (ids) bad_id = ids[res0];
     return fail(c, FAST_EINVAL,
                 "agent %d (id %d): cell %d is outside, not free, unreachable, an exit or taken, "
                 "or the id is outside [0, 2^24), repeated or without a speed; the replicate "
                 "now has no agents",
-                res[0], bad_id, bad_cell);
+                res0, bad_id, bad_cell);
   }
-  R.n = res[1];
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots + r, &n, 4, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_exited + r, &zero, 4, cudaMemcpyHostToDevice, c->stream));
+  R.n = res1;
+  R.n_ids = ids ? -1 : n;
+  const int32_t slots = keep_order ? slots_old + appended : n;
+  words[8] = slots;
+  words[9] = start_step;
+  words[10] = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots + r, words + 8, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_exited + r, words + 10, 4, cudaMemcpyHostToDevice, c->stream));
   // step index and per-step counters
-  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->t, &start_step, 4, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->dig_count, &zero, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->t, words + 9, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->dig_count, words + 10, 4, cudaMemcpyHostToDevice,
+                              c->stream));
   const StepArgs a = args_of(c);
   LAUNCH_TRY(c, step_begin_launch(a, c->stream));
-  // the spatial order of the new agents is made once, before the next step
-  c->resort_pending = true;
+  // the spatial order of new agents is made once, before the next step
+  if (!keep_order) c->resort_pending = true;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->t_host = start_step;
   c->steps_since_place = 0;
   return FAST_OK;
 }
 
-// Every replicate in one call: one upload, all checks queued, one wait.
+// Every replicate in one call: one upload, one launch per stage for all
+// replicates, one wait.
+
 int fast_place_all(fast_ctx* c, const int32_t* counts, const int32_t* cells_by_id,
                    int32_t start_step) {
   if (!c) return FAST_EINVAL;
@@ -903,16 +974,53 @@ int fast_place_all(fast_ctx* c, const int32_t* counts, const int32_t* cells_by_i
   const int64_t total = off[c->n_rep];
   if (total > 0 && !cells_by_id) return fail(c, FAST_EINVAL, "cells_by_id is NULL");
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  // capacities first (a reallocation changes the device descriptors)
+  // the work list below must cover every placed replicate's slots
+  if (c->layout_dirty)
+    if (int e = rebuild_layout(c)) return e;
+  if (int e = batch_buffers(c)) return e;
+  const BatchHost h = batch_host(c);
+  bool any_keep = false, any_clear = false;
+  for (int r = 0; r < c->n_rep; ++r) {
+    const RepHost& R = c->reps[r];
+    const int32_t n = counts[r];
+    BatchRep& b = h.bp[r];
+    b.off = off[r];
+    b.n = n;
+    // the same implicit ids again: agents go back to the slots their ids
+    // hold (as fast_place_agents does)
+    b.keep = (R.placed && n > 0 && n == R.n_ids && n <= R.cap) ? 1 : 0;
+    b.clear = (R.placed && n >= 0) ? 1 : 0;
+    b.n_speed_ids = R.n_speed_ids;
+    b.speed_by_id = R.d_speed_by_id;
+    h.err[3 * r] = INT32_MAX;
+    h.err[3 * r + 1] = 0;
+    h.err[3 * r + 2] = 0;
+    any_keep = any_keep || b.keep;
+    any_clear = any_clear || b.clear;
+  }
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_bp, h.bp, sizeof(BatchRep) * c->n_rep, cudaMemcpyHostToDevice,
+                              c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_berr, h.err, 12 * (size_t)c->n_rep, cudaMemcpyHostToDevice,
+                              c->stream));
+  {
+    const Chunks all = all_chunks(c);
+    const int grid = plan_grid(c, all.n);
+    if (any_keep) LAUNCH_TRY(c, batch_prepare_launch(c->d_reps, all, c->d_bp, grid, c->stream));
+    if (any_clear)
+      LAUNCH_TRY(c, batch_clear_launch(c->d_reps, c->d_nslots, all, c->d_bp, grid, c->stream));
+  }
+  // capacities (a reallocation changes the device descriptors; freeing the
+  // old arrays waits for the clean-up above)
   for (int r = 0; r < c->n_rep; ++r) {
     RepHost& R = c->reps[r];
     const int32_t n = counts[r];
     if (n < 0) continue;
-    if (R.placed && R.cap > 0)
-      LAUNCH_TRY(c, clear_occ_launch(c->d_reps + r, c->d_nslots, r, R.cap, c->stream));
-    if (n > R.cap || !R.placed)
+    if (n > R.cap || !R.placed) {
       if (int e = realloc_slots(c, R, n)) return e;
+      CUDA_TRY(c, cudaMemsetAsync(R.d.cell, 0xFF, (size_t)R.cap * 4, c->stream));
+    }
     R.placed = true;
+    R.n_ids = -1;
   }
   if (c->layout_dirty)
     if (int e = rebuild_layout(c)) return e;
@@ -923,70 +1031,59 @@ int fast_place_all(fast_ctx* c, const int32_t* counts, const int32_t* cells_by_i
     if (int e = alloc_into(c, &c->d_stage, (size_t)total)) return e;
     c->stage_cap = total;
   }
-  if (c->err_cap < 2 * c->n_rep) {
-    dfree(c, c->d_place_errs);
-    c->d_place_errs = nullptr;
-    if (int e = alloc_into(c, &c->d_place_errs, (size_t)2 * c->n_rep)) return e;
-    c->err_cap = 2 * c->n_rep;
-  }
-  if (total > 0)
+  if (total > 0) {
     CUDA_TRY(c, cudaMemcpyAsync(c->d_stage, cells_by_id, (size_t)total * 4,
                                 cudaMemcpyHostToDevice, c->stream));
-  std::vector<int32_t> res(2 * c->n_rep);
-  for (int r = 0; r < c->n_rep; ++r) {
-    res[2 * r] = INT32_MAX;
-    res[2 * r + 1] = 0;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, c->sms * 8));
+    LAUNCH_TRY(c, batch_place_launch(c->d_reps, c->d_stage, total, c->d_bp, c->n_rep,
+                                     c->d_nslots, c->d_berr, grid, c->stream));
   }
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_place_errs, res.data(), res.size() * 4, cudaMemcpyHostToDevice,
+  CUDA_TRY(c, cudaMemcpyAsync(h.err, c->d_berr, 12 * (size_t)c->n_rep, cudaMemcpyDeviceToHost,
                               c->stream));
-  for (int r = 0; r < c->n_rep; ++r) {
-    RepHost& R = c->reps[r];
-    if (counts[r] < 0) continue;
-    CUDA_TRY(c, cudaMemsetAsync(R.d.cell, 0xFF, (size_t)R.cap * 4, c->stream));
-    LAUNCH_TRY(c, place_checked_launch(c->d_reps + r, c->d_stage + off[r], nullptr, counts[r],
-                                       (long long)R.W * R.H, nullptr,
-                                       reinterpret_cast<uint8_t*>(R.d.mvinfo), R.d_speed_by_id,
-                                       R.n_speed_ids, c->d_place_errs + 2 * r, c->stream));
-  }
-  std::vector<int32_t> slots(c->n_rep), exited(c->n_rep);
-  CUDA_TRY(c, cudaMemcpyAsync(res.data(), c->d_place_errs, res.size() * 4, cudaMemcpyDeviceToHost,
+  CUDA_TRY(c, cudaMemcpyAsync(h.slots, c->d_nslots, 4 * (size_t)c->n_rep, cudaMemcpyDeviceToHost,
                               c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(slots.data(), c->d_nslots, 4 * c->n_rep, cudaMemcpyDeviceToHost,
-                              c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(exited.data(), c->d_exited, 4 * c->n_rep, cudaMemcpyDeviceToHost,
+  CUDA_TRY(c, cudaMemcpyAsync(h.exited, c->d_exited, 4 * (size_t)c->n_rep, cudaMemcpyDeviceToHost,
                               c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   int first_bad = -1;
+  bool resort = false;
   for (int r = 0; r < c->n_rep; ++r) {
-    if (counts[r] < 0) continue;
+    const int32_t n = counts[r];
+    if (n < 0) continue;
     RepHost& R = c->reps[r];
-    exited[r] = 0;
-    if (res[2 * r] != INT32_MAX) {
-      LAUNCH_TRY(c, place_rollback_launch(c->d_reps + r, c->d_stage + off[r], counts[r],
+    h.exited[r] = 0;
+    if (h.err[3 * r] != INT32_MAX) {
+      // undo: the replicate is left without agents (every slot written is below n)
+      LAUNCH_TRY(c, place_rollback_launch(c->d_reps + r, c->d_stage + off[r], n,
                                           reinterpret_cast<uint8_t*>(R.d.mvinfo), c->stream));
-      slots[r] = 0;
+      h.slots[r] = 0;
       R.n = 0;
       if (first_bad < 0) first_bad = r;
     } else {
-      slots[r] = counts[r];
-      R.n = res[2 * r + 1];
+      h.slots[r] = h.bp[r].keep ? h.slots[r] + h.err[3 * r + 2] : n;
+      R.n = h.err[3 * r + 1];
+      R.n_ids = n;
+      resort = resort || !h.bp[r].keep;
     }
   }
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots, slots.data(), 4 * c->n_rep, cudaMemcpyHostToDevice,
+  h.misc[0] = start_step;
+  h.misc[1] = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_nslots, h.slots, 4 * (size_t)c->n_rep, cudaMemcpyHostToDevice,
                               c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_exited, exited.data(), 4 * c->n_rep, cudaMemcpyHostToDevice,
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_exited, h.exited, 4 * (size_t)c->n_rep, cudaMemcpyHostToDevice,
                               c->stream));
-  const int32_t zero = 0;
-  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->t, &start_step, 4, cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->dig_count, &zero, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->t, h.misc, 4, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&c->d_ctl->dig_count, h.misc + 1, 4, cudaMemcpyHostToDevice,
+                              c->stream));
   const StepArgs a = args_of(c);
   LAUNCH_TRY(c, step_begin_launch(a, c->stream));
-  c->resort_pending = true;
+  // new agents are put in spatial order once, before the next step
+  if (resort) c->resort_pending = true;
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   c->t_host = start_step;
   c->steps_since_place = 0;
   if (first_bad >= 0) {
-    const int32_t i = res[2 * first_bad];
+    const int32_t i = h.err[3 * first_bad];
     return fail(c, FAST_EINVAL,
                 "replicate %d, agent %d: cell %d is outside, not free, unreachable, an exit or "
                 "taken; the replicates that failed now have no agents",
@@ -1006,7 +1103,8 @@ int fast_readback_all(fast_ctx* c, const int32_t* counts, int32_t* cells_by_id,
     off[r + 1] = off[r] + counts[r];
   }
   const int64_t total = off[c->n_rep];
-  if (int e = check_device_error(c)) return e;
+  if (int e = batch_buffers(c)) return e;
+  const BatchHost h = batch_host(c);
   if (total > 0 && (cells_by_id || desired_by_id)) {
     if (total * 2 > c->gather_cap) {
       dfree(c, c->d_gather);
@@ -1014,14 +1112,23 @@ int fast_readback_all(fast_ctx* c, const int32_t* counts, int32_t* cells_by_id,
       if (int e = alloc_into(c, &c->d_gather, (size_t)total * 2)) return e;
       c->gather_cap = total * 2;
     }
-    CUDA_TRY(c, cudaMemsetAsync(c->d_gather, 0xFF, (size_t)total * 8, c->stream));
+    if (c->layout_dirty)
+      if (int e = rebuild_layout(c)) return e;
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the staging's last use is done
     for (int r = 0; r < c->n_rep; ++r) {
-      RepHost& R = c->reps[r];
-      if (!R.placed || counts[r] == 0) continue;
-      LAUNCH_TRY(c, gather_by_id_launch(c->d_reps + r, c->d_nslots, r, R.cap,
-                                        c->d_gather + off[r], c->d_gather + total + off[r],
-                                        counts[r], c->stream));
+      BatchRep& b = h.bp[r];
+      b.off = off[r];
+      b.n = c->reps[r].placed ? counts[r] : 0;
+      b.keep = b.clear = 0;
+      b.n_speed_ids = 0;
+      b.speed_by_id = nullptr;
     }
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_bp, h.bp, sizeof(BatchRep) * c->n_rep,
+                                cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->d_gather, 0xFF, (size_t)total * 8, c->stream));
+    const Chunks all = all_chunks(c);
+    LAUNCH_TRY(c, batch_gather_launch(c->d_reps, c->d_nslots, all, c->d_bp, c->d_gather,
+                                      c->d_gather + total, plan_grid(c, all.n), c->stream));
     if (cells_by_id)
       CUDA_TRY(c, cudaMemcpyAsync(cells_by_id, c->d_gather, (size_t)total * 4,
                                   cudaMemcpyDeviceToHost, c->stream));
@@ -1029,12 +1136,16 @@ int fast_readback_all(fast_ctx* c, const int32_t* counts, int32_t* cells_by_id,
       CUDA_TRY(c, cudaMemcpyAsync(desired_by_id, c->d_gather + total, (size_t)total * 4,
                                   cudaMemcpyDeviceToHost, c->stream));
   }
-  std::vector<int32_t> exited(c->n_rep);
-  CUDA_TRY(c, cudaMemcpyAsync(exited.data(), c->d_exited, 4 * c->n_rep, cudaMemcpyDeviceToHost,
+  // the control block (device error) and the exit counts come back with the
+  // data: one wait for all of it
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(h.exited, c->d_exited, 4 * (size_t)c->n_rep, cudaMemcpyDeviceToHost,
                               c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (int e = device_error_of(c, *c->h_ctl)) return e;
   if (alive)
-    for (int r = 0; r < c->n_rep; ++r) alive[r] = c->reps[r].placed ? c->reps[r].n - exited[r] : 0;
+    for (int r = 0; r < c->n_rep; ++r)
+      alive[r] = c->reps[r].placed ? c->reps[r].n - h.exited[r] : 0;
   return FAST_OK;
 }
 
@@ -1276,7 +1387,6 @@ int fast_readback(fast_ctx* c, int32_t r, int32_t id_bound, int32_t* cells_by_id
   if (c->poisoned) return FAST_ESTATE;
   if (!rep_ok(c, r) || id_bound < 0) return fail(c, FAST_EINVAL, "bad replicate or id_bound");
   RepHost& R = c->reps[r];
-  if (int e = check_device_error(c)) return e;
   if (id_bound > 0 && (cells_by_id || desired_by_id)) {
     if (id_bound * 2 > c->gather_cap) {
       dfree(c, c->d_gather);
@@ -1294,13 +1404,17 @@ int fast_readback(fast_ctx* c, int32_t r, int32_t id_bound, int32_t* cells_by_id
     if (desired_by_id)
       CUDA_TRY(c, cudaMemcpyAsync(desired_by_id, c->d_gather + id_bound, (size_t)id_bound * 4,
                                   cudaMemcpyDeviceToHost, c->stream));
-    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   }
+  // the control block (device error, counters) and the replicate's exit count
+  // come back with the data: one wait for all of it
+  int32_t* h_exited = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(c->h_ctl) + sizeof(Ctl));
+  CUDA_TRY(c, cudaMemcpyAsync(c->h_ctl, c->d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(h_exited, c->d_exited + r, 4, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const Ctl& h = *c->h_ctl;
+  if (int e = device_error_of(c, h)) return e;
   if (stats) {
-    Ctl h{};
-    int32_t ex = 0;
-    CUDA_TRY(c, cudaMemcpy(&h, c->d_ctl, sizeof h, cudaMemcpyDeviceToHost));
-    CUDA_TRY(c, cudaMemcpy(&ex, c->d_exited + r, 4, cudaMemcpyDeviceToHost));
+    const int32_t ex = *h_exited;
     stats->step = h.t;
     stats->steps_run = c->steps_since_place;
     stats->exited = ex;
@@ -1571,6 +1685,9 @@ void fast_destroy(fast_ctx* c) {
   for (auto& ev : c->ev)
     if (ev) cudaEventDestroy(ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->h_ctl) cudaFreeHost(c->h_ctl);
+  if (c->ev_upload) cudaEventDestroy(c->ev_upload);
+  if (c->h_batch) cudaFreeHost(c->h_batch);
   std::vector<void*> ptrs;
   for (auto& kv : c->live) ptrs.push_back(kv.first);
   for (void* p : ptrs) dfree(c, p);

@@ -52,18 +52,28 @@ int masks_speed_launch(RepDev* d, int64_t cells, int v, int mw, unsigned long lo
 
 // ---------------------------------------------------------------------------
 // Placement: clear the previous agents' marks, then write the new agents.
-__global__ void k_clear_occ(RepDev* rp, const int32_t* n_slots, int rep, int cap) {
+// With slot_of_id, also records the slot each id below n_ids holds (the
+// caller sets the array to -1 first), so that a new placement can keep the
+// storage order.
+__global__ void k_clear_occ(RepDev* rp, const int32_t* n_slots, int rep, int cap,
+                            int32_t* slot_of_id, int n_ids) {
   const RepDev& R = *rp;
   const int n = min(n_slots[rep], cap);
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int c = R.cell[i];
     if (c >= 0) R.rec[c] &= ~(REC_OCC | REC_STA);
     R.cell[i] = -1;
+    if (slot_of_id) {
+      const int id = R.id[i];
+      if (id >= 0 && id < n_ids) slot_of_id[id] = i;
+    }
   }
 }
 
-int clear_occ_launch(RepDev* d, const int32_t* n_slots, int rep, int cap, cudaStream_t s) {
-  k_clear_occ<<<(cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, 256, 0, s>>>(d, n_slots, rep, cap);
+int clear_occ_launch(RepDev* d, const int32_t* n_slots, int rep, int cap, int32_t* slot_of_id,
+                     int n_ids, cudaStream_t s) {
+  k_clear_occ<<<(cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, 256, 0, s>>>(d, n_slots, rep, cap,
+                                                                           slot_of_id, n_ids);
   return 0;
 }
 
@@ -74,46 +84,80 @@ int clear_occ_launch(RepDev* d, const int32_t* n_slots, int rep, int cap, cudaSt
 // found by whichever agent comes second.  Without explicit ids, id i is
 // absent when cells[i] == -1.  err[0] receives the smallest failing index,
 // err[1] the number of agents placed; placed[i] marks the cells this call
-// took, for a roll-back.
+// took, for a roll-back.  With slot_of_id (implicit ids only), agent i goes
+// to the slot its id held before instead (the storage order stays as the
+// last spatial sort left it), or, if it held none, to slot
+// *n_slots_old + err[2]++; an absent agent then takes no slot.
+// One agent of a placement (see k_place_checked); returns whether it counts
+// as present (placed, or refused: err[0] then names it).
+__device__ __forceinline__ bool place_one(const RepDev& R, int i, int c, int id, bool explicit_ids,
+                                          long long n_cells, uint32_t* id_bits, uint8_t* placed,
+                                          const uint8_t* speed_by_id, int n_speed_ids,
+                                          const int32_t* slot_of_id, const int32_t* n_slots_old,
+                                          int32_t* err) {
+  placed[i] = 0;
+  if (slot_of_id && c == -1) return false;
+  int slot = i;
+  if (slot_of_id) {
+    slot = slot_of_id[i];
+    if (slot < 0) slot = *n_slots_old + atomicAdd(&err[2], 1);
+    if (slot >= R.cap) {  // cannot happen with the host's conditions; refused all the same
+      atomicMin(&err[0], i);
+      return false;
+    }
+  }
+  if (speed_by_id) R.speed[slot] = (id >= 0 && id < n_speed_ids) ? speed_by_id[id] : (uint8_t)1;
+  if (!explicit_ids && c == -1) {
+    R.cell[slot] = -1;
+    R.id[slot] = i;
+    R.desired[slot] = -1;
+    return false;
+  }
+  bool ok = c >= 0 && (long long)c < n_cells;
+  // with speeds per agent, every placed id needs one
+  ok = ok && (!speed_by_id || (id >= 0 && id < n_speed_ids));
+  if (ok) {
+    const uint32_t old = atomicOr(&R.rec[c], REC_OCC);
+    if (!(old & REC_OCC)) placed[i] = 1;
+    ok = !(old & REC_OCC) && !rec_exit(old);
+  }
+  if (ok && explicit_ids) {
+    ok = id >= 0 && id < (1 << kMaxIdBits);
+    if (ok) {
+      const uint32_t bit = 1u << (id & 31);
+      ok = !(atomicOr(&id_bits[id >> 5], bit) & bit);
+    }
+  }
+  if (!ok) atomicMin(&err[0], i);
+  R.cell[slot] = ok ? c : -1;
+  R.id[slot] = id;
+  R.desired[slot] = ok ? c : -1;
+  return true;
+}
+
 __global__ void k_place_checked(RepDev* rp, const int32_t* cells, const int32_t* ids, int n,
                                 long long n_cells, uint32_t* id_bits, uint8_t* placed,
-                                const uint8_t* speed_by_id, int n_speed_ids, int32_t* err) {
+                                const uint8_t* speed_by_id, int n_speed_ids,
+                                const int32_t* slot_of_id, const int32_t* n_slots_old,
+                                int32_t* err) {
   const RepDev& R = *rp;
   int present = 0;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int c = cells[i];
-    const int id = ids ? ids[i] : i;
-    placed[i] = 0;
-    if (speed_by_id) R.speed[i] = (id >= 0 && id < n_speed_ids) ? speed_by_id[id] : (uint8_t)1;
-    if (!ids && c == -1) {
-      R.cell[i] = -1;
-      R.id[i] = i;
-      R.desired[i] = -1;
-      continue;
-    }
-    bool ok = c >= 0 && (long long)c < n_cells;
-    // with speeds per agent, every placed id needs one
-    ok = ok && (!speed_by_id || (id >= 0 && id < n_speed_ids));
-    if (ok) {
-      const uint32_t old = atomicOr(&R.rec[c], REC_OCC);
-      if (!(old & REC_OCC)) placed[i] = 1;
-      ok = !(old & REC_OCC) && !rec_exit(old);
-    }
-    if (ok && ids) {
-      ok = id >= 0 && id < (1 << kMaxIdBits);
-      if (ok) {
-        const uint32_t bit = 1u << (id & 31);
-        ok = !(atomicOr(&id_bits[id >> 5], bit) & bit);
-      }
-    }
-    if (!ok) atomicMin(&err[0], i);
-    R.cell[i] = ok ? c : -1;
-    R.id[i] = id;
-    R.desired[i] = ok ? c : -1;
-    ++present;
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    present += place_one(R, i, cells[i], ids ? ids[i] : i, ids != nullptr, n_cells, id_bits,
+                         placed, speed_by_id, n_speed_ids, slot_of_id, n_slots_old, err)
+                   ? 1
+                   : 0;
+  // the block's count first, then one atomic per block (one per warp on a
+  // single word was most of the kernel's time)
+  __shared__ int s_present[32];
   for (int o = 16; o > 0; o >>= 1) present += __shfl_xor_sync(0xffffffffu, present, o);
-  if ((threadIdx.x & 31) == 0 && present) atomicAdd(&err[1], present);
+  if ((threadIdx.x & 31) == 0) s_present[threadIdx.x >> 5] = present;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int sum = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += s_present[w];
+    if (sum) atomicAdd(&err[1], sum);
+  }
 }
 
 // Undoes the occupancy bits a failed placement took.
@@ -127,12 +171,12 @@ __global__ void k_place_rollback(RepDev* rp, const int32_t* cells, int n, const 
 
 int place_checked_launch(RepDev* d, const int32_t* cells, const int32_t* ids, int n,
                          long long n_cells, uint32_t* id_bits, uint8_t* placed,
-                         const uint8_t* speed_by_id, int n_speed_ids, int32_t* err,
-                         cudaStream_t s) {
+                         const uint8_t* speed_by_id, int n_speed_ids, const int32_t* slot_of_id,
+                         const int32_t* n_slots_old, int32_t* err, cudaStream_t s) {
   if (n <= 0) return 0;
-  const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+  const int grid = (n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024;
   k_place_checked<<<grid, 256, 0, s>>>(d, cells, ids, n, n_cells, id_bits, placed, speed_by_id,
-                                       n_speed_ids, err);
+                                       n_speed_ids, slot_of_id, n_slots_old, err);
   return 0;
 }
 
@@ -141,6 +185,122 @@ int place_rollback_launch(RepDev* d, const int32_t* cells, int n, const uint8_t*
   if (n <= 0) return 0;
   const int grid = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
   k_place_rollback<<<grid, 256, 0, s>>>(d, cells, n, placed);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Batched placement and read-back: every replicate of a context in one launch
+// per stage (a launch per replicate and stage cost more than the work of a
+// small replicate).  bp[r] describes replicate r for the call; the chunk
+// kernels walk the work list of all placed replicates' slots.
+
+// Slot-of-id maps (in id2) set to "none" for the replicates that keep their
+// storage order.
+__global__ void k_batch_prepare(RepDev* reps, Chunks ch, const BatchRep* bp) {
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const BatchRep& b = bp[rep];
+    const int s = ch.begin[c] + threadIdx.x;
+    if (b.keep && s < b.n) reps[rep].id2[s] = -1;
+  }
+}
+
+// The previous agents' marks cleared and every slot emptied, as k_clear_occ,
+// for the replicates this call places; the slot-of-id maps filled.
+__global__ void k_batch_clear(RepDev* reps, const int32_t* n_slots, Chunks ch, const BatchRep* bp) {
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const BatchRep& b = bp[rep];
+    if (!b.clear) continue;
+    const RepDev& R = reps[rep];
+    const int s = ch.begin[c] + threadIdx.x;
+    if (s >= R.cap) continue;
+    if (s < min(n_slots[rep], R.cap)) {
+      const int cell = R.cell[s];
+      if (cell >= 0) R.rec[cell] &= ~(REC_OCC | REC_STA);
+      if (b.keep) {
+        const int id = R.id[s];
+        if (id >= 0 && id < b.n) R.id2[id] = s;
+      }
+    }
+    R.cell[s] = -1;
+  }
+}
+
+// The staged agents of all replicates (implicit ids), checked and placed as
+// k_place_checked does; errs[3r..3r+2] as its err for replicate r.
+__global__ void k_batch_place(RepDev* reps, const int32_t* staged, long long total,
+                              const BatchRep* bp, int n_rep, const int32_t* n_slots,
+                              int32_t* errs) {
+  const int lane = threadIdx.x & 31;
+  for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < total;
+       g0 += (long long)gridDim.x * blockDim.x) {  // the same g0 for the whole block
+    const long long g = g0 + threadIdx.x;
+    bool present = false;
+    int rep = 0;
+    if (g < total) {
+      // the replicate whose range holds g: the last with bp[r].off <= g
+      int lo = 0, hi = n_rep - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (bp[mid].off <= g) lo = mid;
+        else hi = mid - 1;
+      }
+      rep = lo;
+      const BatchRep& b = bp[rep];
+      const RepDev& R = reps[rep];
+      const int i = (int)(g - b.off);
+      present = place_one(R, i, staged[g], i, false, (long long)R.W * R.H, nullptr,
+                          reinterpret_cast<uint8_t*>(R.mvinfo), b.speed_by_id, b.n_speed_ids,
+                          b.keep ? R.id2 : nullptr, n_slots + rep, errs + 3 * rep);
+    }
+    // the lanes that place agents of one replicate count them with one atomic
+    const unsigned same = __match_any_sync(0xffffffffu, present ? rep : -1 - lane);
+    if (present && __ffs(same) - 1 == lane) atomicAdd(&errs[3 * rep + 1], __popc(same));
+  }
+}
+
+// Read-back of all replicates: cell and desired cell by id, at bp[r].off + id.
+__global__ void k_batch_gather(const RepDev* reps, const int32_t* n_slots, Chunks ch,
+                               const BatchRep* bp, int32_t* out_cell, int32_t* out_des) {
+  for (int c = blockIdx.x; c < ch.n; c += gridDim.x) {
+    const int rep = ch.rep[c];
+    const BatchRep& b = bp[rep];
+    const RepDev& R = reps[rep];
+    const int s = ch.begin[c] + threadIdx.x;
+    if (s >= min(n_slots[rep], R.cap)) continue;
+    const int cell = R.cell[s];
+    if (cell < 0) continue;
+    const int id = R.id[s];
+    if (id < 0 || id >= b.n) continue;
+    out_cell[b.off + id] = cell;
+    out_des[b.off + id] = R.desired[s];
+  }
+}
+
+int batch_prepare_launch(RepDev* reps, const Chunks& ch, const BatchRep* bp, int grid,
+                         cudaStream_t s) {
+  if (ch.n > 0) k_batch_prepare<<<grid, kChunk, 0, s>>>(reps, ch, bp);
+  return 0;
+}
+
+int batch_clear_launch(RepDev* reps, const int32_t* n_slots, const Chunks& ch, const BatchRep* bp,
+                       int grid, cudaStream_t s) {
+  if (ch.n > 0) k_batch_clear<<<grid, kChunk, 0, s>>>(reps, n_slots, ch, bp);
+  return 0;
+}
+
+int batch_place_launch(RepDev* reps, const int32_t* staged, long long total, const BatchRep* bp,
+                       int n_rep, const int32_t* n_slots, int32_t* errs, int grid,
+                       cudaStream_t s) {
+  if (total > 0) k_batch_place<<<grid, 256, 0, s>>>(reps, staged, total, bp, n_rep, n_slots, errs);
+  return 0;
+}
+
+int batch_gather_launch(const RepDev* reps, const int32_t* n_slots, const Chunks& ch,
+                        const BatchRep* bp, int32_t* out_cell, int32_t* out_des, int grid,
+                        cudaStream_t s) {
+  if (ch.n > 0) k_batch_gather<<<grid, kChunk, 0, s>>>(reps, n_slots, ch, bp, out_cell, out_des);
   return 0;
 }
 

@@ -158,13 +158,33 @@ int masks_launch(const RepDev& host_rep, RepDev* dev_rep, int64_t cells, cudaStr
 int masks_speed_launch(RepDev* dev_rep, int64_t cells, int v, int mw, unsigned long long* out,
                        cudaStream_t s);
 int clear_occ_launch(RepDev* dev_rep, const int32_t* n_slots_dev, int rep, int cap,
-                     cudaStream_t s);
+                     int32_t* slot_of_id, int n_ids, cudaStream_t s);
 int place_checked_launch(RepDev* dev_rep, const int32_t* cells, const int32_t* ids, int n,
                          long long n_cells, uint32_t* id_bits, uint8_t* placed,
-                         const uint8_t* speed_by_id, int n_speed_ids, int32_t* err,
-                         cudaStream_t s);
+                         const uint8_t* speed_by_id, int n_speed_ids, const int32_t* slot_of_id,
+                         const int32_t* n_slots_old, int32_t* err, cudaStream_t s);
 int place_rollback_launch(RepDev* dev_rep, const int32_t* cells, int n, const uint8_t* placed,
                           cudaStream_t s);
+// Batched placement and read-back, one entry per replicate (uploaded by the
+// host for one call).
+struct BatchRep {
+  long long off;               // its first agent in the staged or gathered arrays
+  int32_t n;                   // its ids 0..n-1; -1: not placed by this call
+  int32_t keep;                // 1: agents go back to the slots their ids hold
+  int32_t clear;               // 1: its previous agents are cleared first
+  int32_t n_speed_ids;
+  const uint8_t* speed_by_id;  // nullptr: no speeds per agent
+};
+int batch_prepare_launch(RepDev* reps, const Chunks& ch, const BatchRep* bp, int grid,
+                         cudaStream_t s);
+int batch_clear_launch(RepDev* reps, const int32_t* n_slots, const Chunks& ch, const BatchRep* bp,
+                       int grid, cudaStream_t s);
+int batch_place_launch(RepDev* reps, const int32_t* staged, long long total, const BatchRep* bp,
+                       int n_rep, const int32_t* n_slots, int32_t* errs, int grid,
+                       cudaStream_t s);
+int batch_gather_launch(const RepDev* reps, const int32_t* n_slots, const Chunks& ch,
+                        const BatchRep* bp, int32_t* out_cell, int32_t* out_des, int grid,
+                        cudaStream_t s);
 int gather_by_id_launch(const RepDev* dev_rep, const int32_t* n_slots_dev, int rep, int cap,
                         int32_t* out_cell, int32_t* out_desired, int32_t bound,
                         cudaStream_t s);

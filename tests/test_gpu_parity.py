@@ -352,6 +352,56 @@ def test_place_all_and_readback_all_match_per_replicate_calls(fg, orc):
     assert alive[2] == 0 and alive[0] == int((cells[off[0]:off[1]] >= 0).sum())
 
 
+def test_place_all_mixed_replicates(fg, orc):
+    """One batched placement that leaves one replicate as it is (count -1),
+    places another's read-back state again with some agents moved, removed
+    and brought back (same ids: each agent goes back to its id's storage
+    slot), and gives a third fewer agents (stored by id, then sorted): every
+    replicate then follows the oracle from its own state."""
+    works = wl.config_batch(n_rep=3, seed=9, cells_hi=150 ** 2, agents_hi=2000)
+    ctx = fg.Context(len(works), "fp32_recheck")
+    for r, w in enumerate(works):
+        ctx.init_grid(r, w.cell_type, w.k_S, w.v_m, w.seed)
+    counts = np.array([len(w.cells) for w in works], np.int32)
+    ctx.place_all(counts, np.concatenate([w.cells for w in works]))
+    ctx.step(10)
+    cells, _, _ = ctx.readback_all(counts)
+    t = ctx.readback(0, 0)[2]["step"]
+    off = np.concatenate([[0], np.cumsum(counts)])
+    state = [cells[off[r]:off[r + 1]].copy() for r in range(3)]
+    rng = np.random.default_rng(4)
+    s1 = state[1]
+    present, left = np.flatnonzero(s1 >= 0), np.flatnonzero(s1 < 0)
+    assert len(left) > 0
+    moved = rng.choice(present, 30, replace=False)
+    removed = rng.choice(np.setdiff1d(present, moved), 20, replace=False)
+    back = rng.choice(left, min(10, len(left)), replace=False)
+    free = np.flatnonzero(works[1].cell_type.ravel() == wl.FREE)
+    to = rng.choice(np.setdiff1d(free, s1[present]), len(moved) + len(back), replace=False)
+    s1[moved] = to[:len(moved)]
+    s1[back] = to[len(moved):]
+    s1[removed] = -1
+    state[2] = state[2][:len(state[2]) - 50]
+    new_counts = np.array([-1, len(s1), len(state[2])], np.int32)
+    ctx.place_all(new_counts, np.concatenate([s1, state[2]]), start_step=t)
+    steps = 4
+    ctx.step(steps)
+    read_counts = np.array([len(state[0]), len(s1), len(state[2])], np.int32)
+    got, _, alive = ctx.readback_all(read_counts)
+    roff = np.concatenate([[0], np.cumsum(read_counts)])
+    for r, w in enumerate(works):
+        ids = np.flatnonzero(state[r] >= 0).astype(np.int32)
+        sim = orc.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed)
+        sim.place(state[r][ids], ids=ids)
+        sim.run(t, steps, threads=os.cpu_count() or 1, digests=False)
+        want = np.full(read_counts[r], -1, np.int32)
+        o = sim.cells_by_id()
+        want[:len(o)] = o
+        assert np.array_equal(got[roff[r]:roff[r + 1]], want), r
+        assert alive[r] == int((want >= 0).sum()), r
+    ctx.close()
+
+
 def test_batched_replicates(fg, orc):
     works = wl.config_batch(n_rep=6, seed=3, cells_hi=300 ** 2, agents_hi=6000)
     steps = 30
@@ -507,6 +557,56 @@ def test_recheck_mid_length_queue(fg, orc):
     per_step = g["stats"]["rechecked"] / steps
     assert 2 * sms < per_step <= 8 * sms, per_step
     assert_same(g, run_oracle(orc, w, steps, threads=os.cpu_count() or 1), steps)
+    ctx.close()
+
+
+def test_placing_the_read_back_state_again(fg, orc):
+    """Placing a replicate again with implicit ids and the same count keeps
+    each agent in its id's storage slot (ids without one are added after the
+    others) and skips the sort before the next step.  Run as the end-to-end
+    loop does (place what was read back, step, read back), and with the
+    read-back state changed before it is placed again (agents moved to other
+    free cells, some removed, agents that had left brought back), the cells
+    equal the oracle's sequential run from the same state."""
+    w = wl.config_small_room(W=120, H=90, n=3000, seed=7, v_m=4)
+    n = len(w.cells)
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx.place(0, w.cells)
+    ctx.step(12)  # sorts, and drops agents that left, on the way
+    cells, _, st = ctx.readback(0, n)
+    t = st["step"]
+    free = np.flatnonzero(w.cell_type.ravel() == wl.FREE)
+    rng = np.random.default_rng(3)
+    for case in range(4):
+        new = cells.copy()
+        if case >= 2:
+            present = np.flatnonzero(new >= 0)
+            left = np.flatnonzero(new < 0)
+            assert len(left) > 0
+            moved = rng.choice(present, 40, replace=False)
+            removed = rng.choice(np.setdiff1d(present, moved), 25, replace=False)
+            back = rng.choice(left, min(20, len(left)), replace=False)
+            open_cells = np.setdiff1d(free, new[present])
+            to = rng.choice(open_cells, len(moved) + len(back), replace=False)
+            new[moved] = to[:len(moved)]
+            new[back] = to[len(moved):]
+            new[removed] = -1
+        ids = np.flatnonzero(new >= 0).astype(np.int32)
+        sim = orc.Sim(w.cell_type, v=w.v_m, kS=w.k_S, seed=w.seed)
+        sim.place(new[ids], ids=ids)
+        for k in range(3):  # one step at a time, read back in between
+            ctx.place(0, new, start_step=t)
+            ctx.step(1)
+            new, _, st = ctx.readback(0, n)
+            sim.run(t, 1, threads=os.cpu_count() or 1, digests=False)
+            want = np.full(n, -1, np.int32)
+            o = sim.cells_by_id()
+            want[:len(o)] = o
+            assert np.array_equal(new, want), (case, k)
+            assert st["step"] == t + 1
+            t += 1
+        cells = new
     ctx.close()
 
 
