@@ -149,35 +149,46 @@ def _ptr(a):
 
 
 class _TorchAllocator:
-    """Device memory from PyTorch's caching allocator, kept alive by pointer."""
+    """Device memory from PyTorch's caching allocator, kept alive by pointer;
+    with `limit` (bytes), a request that would take the context's live total
+    above it is refused, as an out-of-memory one is (the library then reports
+    FAST_ENOMEM)."""
 
-    def __init__(self, device):
+    def __init__(self, device, limit=None):
         import torch
 
         self.torch = torch
         self.device = device
+        self.limit = limit
         self.live = {}
+        self.total = 0
         self.alloc_cb = ALLOC_FN(self._alloc)
         self.free_cb = FREE_FN(self._free)
 
     def _alloc(self, nbytes, _user):
+        if self.limit is not None and self.total + int(nbytes) > self.limit:
+            return None
         try:
             t = self.torch.empty(int(nbytes), dtype=self.torch.uint8, device=self.device)
         except Exception:  # out of memory: the library reports FAST_ENOMEM
             return None
         p = t.data_ptr()
         self.live[p] = t
+        self.total += t.numel()
         return p
 
     def _free(self, ptr, _user):
-        self.live.pop(ptr, None)
+        t = self.live.pop(ptr, None)
+        if t is not None:
+            self.total -= t.numel()
 
 
 class Context:
     """One fast_ctx: n replicates stepped together on one CUDA stream."""
 
     def __init__(self, n_replicates: int = 1, precision: str = "fp32_recheck",
-                 reach: str = "l2", stream=None, device=None, torch_memory: bool = True):
+                 reach: str = "l2", stream=None, device=None, torch_memory: bool = True,
+                 memory_limit: int | None = None):
         import torch
 
         if not torch.cuda.is_available():
@@ -185,7 +196,9 @@ class Context:
         self.lib = load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else device
         self.stream = torch.cuda.current_stream(self.device) if stream is None else stream
-        self._alloc = _TorchAllocator(self.device) if torch_memory else None
+        if memory_limit is not None and not torch_memory:
+            raise ValueError("memory_limit needs torch_memory=True (the limit is the allocator's)")
+        self._alloc = _TorchAllocator(self.device, memory_limit) if torch_memory else None
         h = C.c_void_p()
         rc = self.lib.fast_create(
             C.byref(h), n_replicates, PRECISION[precision], REACH[reach],

@@ -277,14 +277,25 @@ void drop_graphs(fast_ctx* c) {
 // (Re)allocates a replicate's per-slot arrays for cap >= n slots.
 int realloc_slots(fast_ctx* c, RepHost& R, int32_t n) {
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  const int32_t cap = std::max(n, std::max(R.cap, 1));
   int32_t* arrs[] = {R.d.id, R.d.cell, R.d.desired, R.d.id2, R.d.cell2};
   for (auto p : arrs) dfree(c, p);
   dfree(c, R.d.prio);
   dfree(c, R.d.mvinfo);
   dfree(c, R.d.speed);
   dfree(c, R.d.speed2);
+  R.d.id = R.d.cell = R.d.desired = R.d.id2 = R.d.cell2 = nullptr;
+  R.d.prio = nullptr;
+  R.d.mvinfo = nullptr;
   R.d.speed = R.d.speed2 = nullptr;
-  const int32_t cap = std::max(n, std::max(R.cap, 1));
+  // no agents until the new arrays are in place (an allocation that fails
+  // below leaves the replicate empty and out of the work lists)
+  R.placed = false;
+  R.n = 0;
+  R.n_ids = -1;
+  R.cap = 0;
+  R.d.cap = 0;
+  c->layout_dirty = true;
   if (int e = alloc_into(c, &R.d.id, cap)) return e;
   if (int e = alloc_into(c, &R.d.cell, cap)) return e;
   if (int e = alloc_into(c, &R.d.desired, cap)) return e;
@@ -752,6 +763,13 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
   R.d.rec = nullptr;
   R.d.mask = nullptr;
   R.d.claim[0] = R.d.claim[1] = nullptr;
+  // until the new arrays are in place the replicate has no grid and no
+  // agents, and the work lists are rebuilt without it (so an allocation that
+  // fails below leaves a state that later calls refuse, not freed memory)
+  R.grid_set = false;
+  R.placed = false;
+  R.n_ids = -1;
+  c->layout_dirty = true;
   R.W = g->width;
   R.H = g->height;
   R.v = g->v_m;

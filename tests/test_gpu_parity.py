@@ -352,6 +352,32 @@ def test_place_all_and_readback_all_match_per_replicate_calls(fg, orc):
     assert alive[2] == 0 and alive[0] == int((cells[off[0]:off[1]] >= 0).sum())
 
 
+def test_allocation_failure_is_reported_and_recoverable(fg, orc):
+    """The allocator refuses device memory (a 64 MB limit on the context,
+    below what a 3000x3000 grid needs: its records fit, its line-of-sight
+    masks do not): fast_init_grid returns FAST_ENOMEM, the replicate is left
+    without a grid (placing agents is refused), and the same context then
+    runs a small grid exactly as the oracle does."""
+    ctx = fg.Context(1, "fp32_recheck", memory_limit=64 << 20)
+    big = wl.room(3000, 3000)
+    wl.add_exit(big, "bottom", 1500, 4)
+    with pytest.raises(fg.FastError) as e:
+        ctx.init_grid(0, big, 1.2, 4, 0)
+    assert e.value.code == -3
+    with pytest.raises(fg.FastError) as e:
+        ctx.place(0, np.array([3001 + 5], np.int32))
+    assert e.value.code == -2
+    w = wl.config_small_room(W=60, H=50, n=500, seed=1, v_m=4)
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx.place(0, w.cells)
+    steps = 5
+    ctx.step(steps)
+    cells, _, st = ctx.readback(0, len(w.cells))
+    assert st["step"] == steps
+    assert np.array_equal(cells, run_oracle(orc, w, steps)["cells"])
+    ctx.close()
+
+
 def test_place_all_mixed_replicates(fg, orc):
     """One batched placement that leaves one replicate as it is (count -1),
     places another's read-back state again with some agents moved, removed
