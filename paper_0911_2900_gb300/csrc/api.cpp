@@ -280,12 +280,10 @@ int realloc_slots(fast_ctx* c, RepHost& R, int32_t n) {
   const int32_t cap = std::max(n, std::max(R.cap, 1));
   int32_t* arrs[] = {R.d.id, R.d.cell, R.d.desired, R.d.id2, R.d.cell2};
   for (auto p : arrs) dfree(c, p);
-  dfree(c, R.d.prio);
   dfree(c, R.d.mvinfo);
   dfree(c, R.d.speed);
   dfree(c, R.d.speed2);
   R.d.id = R.d.cell = R.d.desired = R.d.id2 = R.d.cell2 = nullptr;
-  R.d.prio = nullptr;
   R.d.mvinfo = nullptr;
   R.d.speed = R.d.speed2 = nullptr;
   // no agents until the new arrays are in place (an allocation that fails
@@ -301,7 +299,6 @@ int realloc_slots(fast_ctx* c, RepHost& R, int32_t n) {
   if (int e = alloc_into(c, &R.d.desired, cap)) return e;
   if (int e = alloc_into(c, &R.d.id2, cap)) return e;
   if (int e = alloc_into(c, &R.d.cell2, cap)) return e;
-  if (int e = alloc_into(c, &R.d.prio, cap)) return e;
   if (int e = alloc_into(c, &R.d.mvinfo, cap)) return e;
   if (R.speed_set) {
     if (int e = alloc_into(c, &R.d.speed, cap)) return e;

@@ -53,7 +53,6 @@ struct RepDev {
   int32_t* desired;                 // [cap]
   int32_t* id2;                     // [cap]  re-sort buffers
   int32_t* cell2;                   // [cap]
-  unsigned long long* prio;         // [cap]  movement priority this step
   uint32_t* mvinfo;                 // [cap]  scratch of the re-sort (desired cells)
   // maximum speed per agent (Sec. 2's benchmark gives every agent the same
   // one; the model allows one per agent): speed[slot] in 1..5, or nullptr
