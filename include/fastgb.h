@@ -175,7 +175,9 @@ int fast_create(fast_ctx** out, int32_t n_replicates, int32_t precision, int32_t
  * wall.  With grid->static_field the caller's field replaces the computed
  * one (its +inf cells are the walls so added).  Errors: FAST_EINVAL (types,
  * size, v_m, k_S, no exit, distance too long for the 15-bit record fields, a
- * static_field value that is not of the form above), FAST_ENOMEM,
+ * static_field value that is not of the form above), FAST_ENOMEM (the
+ * replicate is then left without a grid and without agents; a later call on
+ * it is refused with FAST_ESTATE until a fast_init_grid succeeds),
  * FAST_ECUDA. */
 int fast_init_grid(fast_ctx* ctx, int32_t replicate, const fast_grid_desc* grid);
 
