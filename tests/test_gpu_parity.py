@@ -527,9 +527,10 @@ def test_batched_form_full_size(fg, orc):
     1e3..1e5 agents, v_m 1..5) in one context, autotuned, the step loop as
     one graph launch as the benchmark runs it: every replicate's per-step
     desired and cell digests and its final positions and desired cells equal
-    the oracle's, run from the same start, for 40 steps."""
+    the oracle's, run from the same start, for the configuration's 396
+    steps."""
     works = wl.config_batch()
-    steps = 40
+    steps = 396
     ctx = fg.Context(len(works), "fp32_recheck")
     ctx.set_option("digests", 1)
     for r, w in enumerate(works):
