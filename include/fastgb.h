@@ -307,8 +307,9 @@ int fast_reach_union(fast_ctx* ctx, int32_t replicate, int64_t* cells);
  * beyond).  Every call on a device shares that array, so calls that can
  * overlap on the GPU race; order them on one stream.  The first call on a
  * device looks up the array's device address (make it before any stream
- * capture).  FAST_ESTATE if the context has not run fast_step or
- * fast_plan_only since its last fast_init_grid / fast_place_agents. */
+ * capture).  FAST_ESTATE if the replicate has no agents, or if an option
+ * that changes the context's work lists (the bucket side) was set since the
+ * last placement, fast_step or fast_plan_only. */
 int fast_plan_noalloc(fast_ctx* ctx, int32_t replicate, int32_t step, int32_t id_bound,
                       int32_t* desired_by_id_dev);
 
