@@ -964,7 +964,8 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
   LAUNCH_TRY(c, step_begin_launch(a, c->stream));
   // the spatial order of new agents is made once, before the next step
   if (!keep_order) c->resort_pending = true;
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // no wait here: what is still queued reads the pinned staging words 8..10,
+  // which only the next placement rewrites, after its own wait
   c->t_host = start_step;
   c->steps_since_place = 0;
   return FAST_OK;
@@ -1094,7 +1095,8 @@ int fast_place_all(fast_ctx* c, const int32_t* counts, const int32_t* cells_by_i
   LAUNCH_TRY(c, step_begin_launch(a, c->stream));
   // new agents are put in spatial order once, before the next step
   if (resort) c->resort_pending = true;
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  // no wait here: what is still queued reads the pinned slot, exit and step
+  // words, which only the next batched call rewrites, after its own wait
   c->t_host = start_step;
   c->steps_since_place = 0;
   if (first_bad >= 0) {
