@@ -119,3 +119,27 @@ def test_checked_build_exports_the_same_boundary():
     assert not missing, missing
     rel.fast_build_checked.restype = chk.fast_build_checked.restype = C.c_int
     assert rel.fast_build_checked() == 0 and chk.fast_build_checked() == 1
+
+
+def test_memory_limit_accounting():
+    """The binding's allocator refuses a request that would take the live
+    total above the context's memory limit (the library then reports
+    FAST_ENOMEM), and counts freed memory back; CPU tensors stand in for
+    device memory here (no kernel runs)."""
+    import ctypes as C
+
+    from paper_0911_2900_gb300 import _TorchAllocator
+
+    a = _TorchAllocator("cpu", limit=1000)
+    p1 = a._alloc(600, None)
+    assert p1 and a.total == 600
+    assert a._alloc(500, None) is None and a.total == 600
+    p2 = a._alloc(400, None)
+    assert p2 and a.total == 1000
+    a._free(p1, None)
+    assert a.total == 400
+    assert a._alloc(500, None) and a.total == 900
+    a._free(C.c_void_p(12345).value, None)  # an unknown pointer is ignored
+    assert a.total == 900
+    unlimited = _TorchAllocator("cpu")
+    assert unlimited._alloc(1 << 20, None) and unlimited.total == 1 << 20
