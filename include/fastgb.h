@@ -197,7 +197,11 @@ int fast_init_grid(fast_ctx* ctx, int32_t replicate, const fast_grid_desc* grid)
 int fast_set_speeds(fast_ctx* ctx, int32_t replicate, int32_t n_ids, const uint8_t* speed_by_id);
 
 /* Places n agents of one replicate (replacing any previous ones).
- * cells: host [n] distinct free, reachable, non-exit cells (NULL: error);
+ * cells: host [n] distinct free, reachable, non-exit cells; NULL: a seeded
+ * uniform placement -- ids 0..n-1 on n distinct cells drawn uniformly from
+ * the free, reachable, non-exit cells with a generator started from the
+ * grid's seed, so the same grid, seed and n always give the same cells (ids
+ * must then be NULL, and n at most the number of such cells);
  * ids: host [n] distinct ids in [0, 2^24); NULL: agent i has id i, and
  * cells[i] == -1 means there is no agent with id i (so the cells-by-id array
  * that fast_readback writes can be placed again as it is);

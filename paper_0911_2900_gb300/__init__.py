@@ -268,6 +268,13 @@ class Context:
                                                int(start_step)), "fast_place_agents")
         self.id_bound[rep] = (int(i.max()) + 1 if len(c) else 0) if i is not None else len(c)
 
+    def place_uniform(self, rep: int, n: int, start_step: int = 0):
+        """Ids 0..n-1 on n distinct free, reachable cells drawn uniformly,
+        from the grid's seed (fast_place_agents with no cells)."""
+        self._check(self.lib.fast_place_agents(self.h, rep, int(n), None, None, int(start_step)),
+                    "fast_place_agents")
+        self.id_bound[rep] = int(n)
+
     def place_all(self, counts, cells_by_id, start_step: int = 0):
         """Every replicate at once: counts[r] ids of replicate r (-1: leave it),
         cells_by_id the concatenation of the replicates' cells-by-id arrays."""

@@ -48,6 +48,8 @@ struct RepHost {
   int32_t cap = 0;                 // agent slots allocated
   int32_t n = 0;                   // agents placed
   int32_t n_ids = -1;              // ids of the last placement if they were implicit (0..n-1)
+  std::vector<uint64_t> eligible;  // bit i: cell i may hold an agent (free, reachable)
+  int64_t n_eligible = 0;
   uint32_t speed_set = 0;          // speeds given per agent (bit s-1: speed s), 0: all v
   uint8_t* d_speed_by_id = nullptr;  // device copy of the speeds by id
   int32_t n_speed_ids = 0;
@@ -620,6 +622,44 @@ int batch_buffers(fast_ctx* c) {
 }
 }  // namespace
 
+namespace {
+// Seeded uniform placement: n distinct cells drawn uniformly from the
+// replicate's eligible cells (free, reachable, not an exit) in one pass of
+// selection sampling (Knuth's Algorithm S: keep a cell with probability
+// needed / left), then handed to ids 0..n-1 in a random order (Fisher-Yates
+// shuffle).  Both draw from one splitmix64 stream (Steele, Lea and Flood's
+// generator) started from the grid's seed, so one (grid, seed, n) always
+// gives one placement.  Requires n <= R.n_eligible.
+void uniform_cells(const RepHost& R, int32_t n, std::vector<int32_t>& out) {
+  uint64_t state = R.seed;
+  auto next = [&state]() {
+    state += 0x9E3779B97F4A7C15ull;
+    uint64_t z = state;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  };
+  out.clear();
+  out.reserve((size_t)n);
+  int64_t left = R.n_eligible, need = n;
+  for (size_t w = 0; w < R.eligible.size() && need > 0; ++w) {
+    uint64_t bits = R.eligible[w];
+    while (bits && need > 0) {
+      const int64_t i = (int64_t)(w << 6) + __builtin_ctzll(bits);
+      bits &= bits - 1;
+      const double u = (double)(next() >> 11) * 0x1.0p-53;  // uniform in [0, 1)
+      if (u * (double)left < (double)need) {
+        out.push_back((int32_t)i);
+        --need;
+      }
+      --left;
+    }
+  }
+  for (int64_t k = (int64_t)out.size() - 1; k > 0; --k)
+    std::swap(out[(size_t)k], out[(size_t)(next() % (uint64_t)(k + 1))]);
+}
+}  // namespace
+
 // ===========================================================================
 extern "C" {
 
@@ -743,6 +783,14 @@ int fast_init_grid(fast_ctx* c, int32_t r, const fast_grid_desc* g) {
       return fail(c, FAST_EINVAL, "distance to the nearest exit too long at cell %lld", (long long)i);
     rec[i] = (uint32_t)a[i] | ((uint32_t)b[i] << 15);
   }
+  // the cells a seeded uniform placement draws from
+  R.eligible.assign((size_t)((C + 63) / 64), 0ull);
+  R.n_eligible = 0;
+  for (int64_t i = 0; i < C; ++i)
+    if (g->cell_type[i] == FAST_CELL_FREE && a[i] >= 0) {
+      R.eligible[(size_t)(i >> 6)] |= 1ull << (i & 63);
+      ++R.n_eligible;
+    }
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   // (re)allocate the per-cell arrays
   dfree(c, R.d.rec);
@@ -872,8 +920,18 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
   RepHost& R = c->reps[r];
   if (!R.grid_set) return fail(c, FAST_ESTATE, "grid of replicate %d not set", r);
   if (n < 0 || n > (1 << kMaxIdBits)) return fail(c, FAST_EINVAL, "agent count %d out of range", n);
-  if (n > 0 && !cells) return fail(c, FAST_EINVAL, "cells is NULL");
   if (start_step < 0) return fail(c, FAST_EINVAL, "start_step < 0");
+  // no cells: a seeded uniform placement of ids 0..n-1
+  const bool uniform = n > 0 && !cells;
+  std::vector<int32_t> drawn;
+  if (uniform) {
+    if (ids) return fail(c, FAST_EINVAL, "a uniform placement (cells NULL) takes no ids");
+    if (n > R.n_eligible)
+      return fail(c, FAST_EINVAL, "%d agents but only %lld free reachable cells", n,
+                  (long long)R.n_eligible);
+    uniform_cells(R, n, drawn);
+    cells = drawn.data();
+  }
   const int64_t C = (int64_t)R.W * R.H;
 
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -881,7 +939,7 @@ int fast_place_agents(fast_ctx* c, int32_t r, int32_t n, const int32_t* cells, c
   // every agent goes back to the slot its id holds, so the storage order the
   // last spatial sort made stays, and no sort is needed before the next step
   // (agents move at most a few cells per step).
-  const bool keep_order = R.placed && !ids && n > 0 && n == R.n_ids && n <= R.cap;
+  const bool keep_order = R.placed && !ids && !uniform && n > 0 && n == R.n_ids && n <= R.cap;
   int32_t* slot_of_id = keep_order ? R.d.id2 : nullptr;  // free scratch of cap slots here
   if (keep_order) CUDA_TRY(c, cudaMemsetAsync(slot_of_id, 0xFF, (size_t)n * 4, c->stream));
   // clear the previous agents' occupancy marks

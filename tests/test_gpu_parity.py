@@ -378,6 +378,53 @@ def test_allocation_failure_is_reported_and_recoverable(fg, orc):
     ctx.close()
 
 
+def test_seeded_uniform_placement(fg, orc):
+    """fast_place_agents without cells places ids 0..n-1 on distinct free
+    cells from which an exit can be reached, drawn from the grid's seed: the
+    same grid, seed and count give the same cells, another seed others; a
+    walled-in pocket of free cells gets no agent; more agents than such cells
+    are refused; and the run from the drawn cells equals the oracle's."""
+    t = wl.room(80, 60)
+    wl.add_exit(t, "bottom", 40, 4)
+    t[20:31, 20] = wl.WALL  # a closed pocket of 9x9 free cells
+    t[20:31, 30] = wl.WALL
+    t[20, 20:31] = wl.WALL
+    t[30, 20:31] = wl.WALL
+    pocket = np.zeros(t.shape, bool)
+    pocket[21:30, 21:30] = True
+    eligible = ((t == wl.FREE) & ~pocket).ravel()
+    n_el = int(eligible.sum())
+    n = int(0.9 * n_el)
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.init_grid(0, t, 1.2, 4, 123)
+    ctx.place_uniform(0, n)
+    cells, _, _ = ctx.readback(0, n)
+    assert (cells >= 0).all() and len(np.unique(cells)) == n
+    assert eligible[cells].all()
+    ctx.place_uniform(0, n)
+    assert np.array_equal(ctx.readback(0, n)[0], cells)
+    other = fg.Context(1, "fp32_recheck")
+    other.init_grid(0, t, 1.2, 4, 124)
+    other.place_uniform(0, n)
+    assert not np.array_equal(other.readback(0, n)[0], cells)
+    other.close()
+    with pytest.raises(fg.FastError) as e:
+        ctx.place_uniform(0, n_el + 1)
+    assert e.value.code == -1
+    ctx.place_uniform(0, n)
+    steps = 15
+    ctx.step(steps)
+    got = ctx.readback(0, n)[0]
+    sim = orc.Sim(t, v=4, kS=1.2, seed=123)
+    sim.place(cells)
+    sim.run(0, steps, threads=os.cpu_count() or 1, digests=False)
+    want = np.full(n, -1, np.int32)
+    o = sim.cells_by_id()
+    want[:len(o)] = o
+    assert np.array_equal(got, want)
+    ctx.close()
+
+
 def test_place_all_mixed_replicates(fg, orc):
     """One batched placement that leaves one replicate as it is (count -1),
     places another's read-back state again with some agents moved, removed
