@@ -137,6 +137,9 @@ typedef struct {
                            /* their agents did not fit one shared-memory tile  */
   int64_t movers;          /* agents handed to the movement rounds, all steps  */
   int64_t footprint_cells; /* their footprint cells, all steps                 */
+  int64_t diag_flips;      /* the last fast_precision_report_run: FP32-only     */
+                           /* choices that differ from the FP64 rule (0: none) */
+  double diag_max_abs_dp;  /* its largest |p32 - p64| over the candidates       */
 } fast_stats;
 
 typedef struct {

@@ -45,7 +45,8 @@ class Stats(C.Structure):
                 ("exited", C.c_int32), ("agent_steps", C.c_int64), ("rechecked", C.c_int64),
                 ("move_rounds", C.c_int64), ("max_rounds", C.c_int32), ("last_rounds", C.c_int32),
                 ("kernel_launches", C.c_int64), ("tile_fallbacks", C.c_int64),
-                ("movers", C.c_int64), ("footprint_cells", C.c_int64)]
+                ("movers", C.c_int64), ("footprint_cells", C.c_int64),
+                ("diag_flips", C.c_int64), ("diag_max_abs_dp", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

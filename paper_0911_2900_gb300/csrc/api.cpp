@@ -1503,6 +1503,10 @@ int fast_readback(fast_ctx* c, int32_t r, int32_t id_bound, int32_t* cells_by_id
     stats->tile_fallbacks = (int64_t)h.tile_fallbacks;
     stats->movers = (int64_t)h.movers_total;
     stats->footprint_cells = (int64_t)h.foot_total;
+    stats->diag_flips = (int64_t)h.flips;
+    float mdp;
+    std::memcpy(&mdp, &h.max_dp_bits, 4);
+    stats->diag_max_abs_dp = mdp;
   }
   return FAST_OK;
 }

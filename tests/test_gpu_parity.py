@@ -611,9 +611,28 @@ def test_precision_form_full_length(fg, orc):
     assert rep["flagged"] < 0.01 * rep["agents"]
     ctx.step(steps)
     cells, des, st = ctx.readback(0, len(w.cells))
+    # the read-back's stats carry the report's diagnostics
+    assert st["diag_flips"] == rep["flips"] and st["diag_max_abs_dp"] == rep["max_abs_dp"]
     dc, dd = ctx.digests(0, steps)
     o = run_oracle(orc, w, steps, threads=os.cpu_count() or 1)
     assert_same(dict(cells=cells, desired=des, stats=st, dig_cell=dc, dig_des=dd), o, steps)
+
+
+def test_stats_carry_the_precision_report(fg):
+    """fast_readback's stats give the last precision report's FP32-only
+    flip count and largest |p32 - p64| (zero before any report)."""
+    w = wl.config_small_room(W=120, H=90, n=4000, seed=8, v_m=5)
+    ctx = fg.Context(1, "fp32_recheck")
+    ctx.init_grid(0, w.cell_type, w.k_S, w.v_m, w.seed)
+    ctx.place(0, w.cells)
+    ctx.step(3)
+    st = ctx.readback(0, 0)[2]
+    assert st["diag_flips"] == 0 and st["diag_max_abs_dp"] == 0.0
+    rep = ctx.precision_report()
+    st = ctx.readback(0, 0)[2]
+    assert st["diag_flips"] == rep["flips"]
+    assert st["diag_max_abs_dp"] == rep["max_abs_dp"] > 0.0
+    ctx.close()
 
 
 def test_recheck_mid_length_queue(fg, orc):
